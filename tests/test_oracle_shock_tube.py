@@ -1,0 +1,94 @@
+"""Pins of the exact Riemann solver (textbook star state, jump conditions)
+and of the oracle's shock tubes (Sec. V) against it."""
+import math
+
+import numpy as np
+import pytest
+
+import lbm_inputs as li
+from oracle import oracle as ora
+from oracle import riemann
+
+
+def test_sod_star_state_matches_textbook(golden):
+    vals = {rw[0]: float(rw[1]) for rw in golden("sod_toro_test1.txt")}
+    left, right, gamma = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4
+    ps, us = riemann.star_state(left, right, gamma)
+    assert abs(ps - vals["p_star"]) < 1e-5
+    assert abs(us - vals["u_star"]) < 1e-5
+    xi = np.array([us - 1e-9, us + 1e-9])
+    rho, u, p = riemann.sample(left, right, gamma, xi)
+    assert abs(rho[0] - vals["rho_star_L"]) < 1e-5
+    assert abs(rho[1] - vals["rho_star_R"]) < 1e-5
+
+
+@pytest.mark.parametrize("gamma", [1.1, 1.4, 1.67])
+def test_riemann_jump_conditions(gamma):
+    """Rankine-Hugoniot across the right shock; isentropy and the Riemann
+    invariant u + 2a/(gamma-1) across the left rarefaction."""
+    left, right = (3.0, 0.0, 2.5), (0.7, 0.0, 0.4)
+    ps, us = riemann.star_state(left, right, gamma)
+    rho, u, p = riemann.sample(left, right, gamma, np.array([us + 1e-9, 1e6]))
+    r1, u1, p1 = rho[0], u[0], p[0]
+    r0, u0, p0 = rho[1], u[1], p[1]
+    # shock speed from mass conservation, then momentum and energy fluxes
+    S = (r1 * u1 - r0 * u0) / (r1 - r0)
+    m = r0 * (u0 - S)
+    assert abs(m * (u1 - u0) + (p1 - p0)) < 1e-10
+    e = lambda r, uu, pp: pp / ((gamma - 1) * r) + 0.5 * (uu - S) ** 2
+    assert abs(e(r1, u1, p1) + p1 / r1 - e(r0, u0, p0) - p0 / r0) < 1e-10
+    # left rarefaction fan: sample inside it
+    al = math.sqrt(gamma * left[2] / left[0])
+    a_s = al * (ps / left[2]) ** ((gamma - 1) / (2 * gamma))
+    fan = np.linspace(-al + 1e-6, us - a_s - 1e-6, 7)
+    rho, u, p = riemann.sample(left, right, gamma, fan)
+    np.testing.assert_allclose(p / rho ** gamma, left[2] / left[0] ** gamma, rtol=1e-12)
+    a = np.sqrt(gamma * p / rho)
+    np.testing.assert_allclose(u + 2 * a / (gamma - 1), 2 * al / (gamma - 1), rtol=1e-12)
+
+
+def test_symmetric_collision_has_zero_star_velocity():
+    ps, us = riemann.star_state((1.0, 0.5, 1.0), (1.0, -0.5, 1.0), 1.4)
+    assert abs(us) < 1e-14 and ps > 1.0
+
+
+def shock_tube_l1(nx, lat=ora.D2Q37, t=0.1504):
+    """The paper's shock tube (Sec. V): rho 4|1, T 1|1, u = 0, gamma = 1.4
+    (delta = 3 in 2D), tau = 2/3, open x ends, periodic y; a 1-cell-high
+    strip (uniform in y) is the same computation as any Ny."""
+    _, _, r = ora.lattice_info(lat)
+    steps = int(round(t * nx * r))
+    rho, u, T = li.sod_fields(nx, 1, left=(4.0, 0.0, 1.0), right=(1.0, 0.0, 1.0))
+    s = ora.Oracle(lat, 1.4, 2.0 / 3.0, 2.0 / 3.0, (nx, 1), bc=(ora.ZERO_GRADIENT, ora.PERIODIC))
+    s.init(rho, u, T)
+    s.step(steps)
+    R, U, TT = s.moments()
+    er, eu, eT = riemann.shock_tube_profile((4.0, 0.0, 4.0), (1.0, 0.0, 1.0), 1.4, nx,
+                                            riemann.lattice_time(steps, nx, r))
+    return np.array([riemann.l1_error(R, er), riemann.l1_error(U[0], eu), riemann.l1_error(TT, eT)])
+
+
+def test_paper_shock_tube_converges_to_exact_solution():
+    """The paper gives no numbers (its figure is missing), so the absolute
+    L1 level is not pinned; its behaviour is: the L1 error of rho, u, T
+    against the exact Riemann solution falls as the grid is refined at fixed t."""
+    e = [shock_tube_l1(nx) for nx in (500, 1000, 2000)]
+    assert np.all(e[1] < e[0]) and np.all(e[2] < e[1]), e
+    # and is small in absolute terms at the paper's resolution
+    assert e[1][0] < 0.02 and e[1][1] < 0.01 and e[1][2] < 0.01
+
+
+def test_classic_sod_tube_close_to_exact():
+    """Classic Sod states on 1000 cells, tau = 0.6, 180 steps (t = 0.1504)."""
+    nx, steps = 1000, 180
+    _, _, r = ora.lattice_info(ora.D2Q37)
+    rho, u, T = li.sod_fields(nx, 1)
+    s = ora.Oracle(ora.D2Q37, 1.4, 0.6, 0.6, (nx, 1), bc=(ora.ZERO_GRADIENT, ora.PERIODIC))
+    s.init(rho, u, T)
+    s.step(steps)
+    R, U, TT = s.moments()
+    er, eu, eT = riemann.shock_tube_profile((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, nx,
+                                            riemann.lattice_time(steps, nx, r))
+    assert riemann.l1_error(R, er) < 0.005
+    assert riemann.l1_error(U[0], eu) < 0.005
+    assert riemann.l1_error(TT, eT) < 0.008
