@@ -1,0 +1,389 @@
+"""Benchmark of the fused f+g stream-collide step (MLUPS and % of HBM roofline).
+
+Default workload: D2Q37, FP32 compute and storage, periodic 4096 x 4096 box,
+rho = 1 + 1% random Fourier modes, u = 8 random Fourier modes of amplitude
+0.02, T = 1, gamma = 1.4, tau_f = 0.55, tau_g = 0.7.  One bench step = one
+solve of 200 lattice time steps: init from resident FP64 fields, 200 fused
+steps, moments back to resident FP64 fields.  MLUPS counts cell updates of
+both populations (cells x 200 per bench step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload periodic2d|periodic2d_f64|periodic3d|sod2d_s16|...]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica of the workload (the path has no exchange step on one
+grid per GPU), so the value is the sum over ranks ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbm_inputs as li  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+
+WORKLOADS = {
+    # name: lattice, prec, shape, gamma, tau_f, tau_g, steps per solve, fields
+    "periodic2d": dict(lattice=0, prec="f32", shape=(4096, 4096), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=200,
+                       fields="fourier2d",
+                       desc="D2Q37 FP32 periodic 4096x4096, 8-mode Fourier fields (seeds 1,2), gamma 1.4, "
+                            "tau_f 0.55, tau_g 0.7, 200 steps per solve"),
+    "periodic2d_f64": dict(lattice=0, prec="f64", shape=(4096, 4096), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=20,
+                           fields="fourier2d",
+                           desc="D2Q37 FP64 periodic 4096x4096, same fields, 20 steps per solve"),
+    "periodic2d_s16f": dict(lattice=0, prec="f32_s16f", shape=(4096, 4096), gamma=1.4, tau_f=0.55, tau_g=0.7,
+                            steps=200, fields="fourier2d",
+                            desc="D2Q37 FP32 compute, FP16 deviation storage, periodic 4096x4096, 200 steps"),
+    "periodic2d_s16bf": dict(lattice=0, prec="f32_s16bf", shape=(4096, 4096), gamma=1.4, tau_f=0.55, tau_g=0.7,
+                             steps=200, fields="fourier2d",
+                             desc="D2Q37 FP32 compute, BF16 deviation storage, periodic 4096x4096, 200 steps"),
+    "periodic2d_small": dict(lattice=0, prec="f32", shape=(1024, 1024), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=20,
+                             fields="fourier2d",
+                             desc="D2Q37 FP32 periodic 1024x1024 (profiling case, 0.6 GB state > L2), 20 steps"),
+    "periodic2d_f64_small": dict(lattice=0, prec="f64", shape=(1024, 1024), gamma=1.4, tau_f=0.55, tau_g=0.7,
+                                 steps=10, fields="fourier2d",
+                                 desc="D2Q37 FP64 periodic 1024x1024 (profiling case), 10 steps"),
+    "periodic3d_small": dict(lattice=1, prec="f32", shape=(96, 96, 96), gamma=1.4, tau_f=0.6, tau_g=0.6, steps=10,
+                             fields="fourier3d",
+                             desc="D3Q107 FP32 periodic 96^3 (profiling case, 0.8 GB state > L2), 10 steps"),
+    "periodic3d": dict(lattice=1, prec="f32", shape=(256, 256, 256), gamma=1.4, tau_f=0.6, tau_g=0.6, steps=100,
+                       fields="fourier3d",
+                       desc="D3Q107 FP32 periodic 256^3, 8-mode Fourier rho/u/T (seeds 3,4,5), gamma 1.4, "
+                            "tau 0.6, 100 steps per solve"),
+}
+
+
+# ---------------------------------------------------------------------------
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_fields(wl, shape):
+    if wl["fields"] == "fourier2d":
+        return li.fourier_fields(shape, seed_u=1, seed_rho=2)
+    if wl["fields"] == "fourier3d":
+        return li.fourier_fields(shape, seed_u=3, seed_rho=4, seed_T=5)
+    raise ValueError(wl["fields"])
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1608_06345_gb300", "csrc")
+    for f in ("kernels.cuh", "launch_impl.cuh", "step_inst.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    rec = d.get(key)
+    if not rec or rec.get("src_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(wl, seconds_target=15.0, min_steps=1):
+    """Time the FP64 oracle on a bounded sample of the workload: the same
+    recipe on a smaller box (1024^2 in 2D, 96^3 in 3D), steps chosen for
+    about `seconds_target` of CPU work.  Returns (MLUPS, cores, description)."""
+    from oracle import oracle as ora
+    shape = (1024, 1024) if len(wl["shape"]) == 2 else (96, 96, 96)
+    rho, u, T = make_fields(wl, shape)
+    s = ora.Oracle(wl["lattice"], wl["gamma"], wl["tau_f"], wl["tau_g"], shape)
+    s.init(rho, u, T)
+    t0 = time.perf_counter()
+    s.step(1)
+    one = time.perf_counter() - t0
+    steps = max(min_steps, int(seconds_target / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    N = int(np.prod(shape))
+    mlups = N * steps / dt / 1e6
+    desc = f"FP64 oracle, {'x'.join(map(str, shape))} periodic box of the same recipe, {steps} steps"
+    return mlups, ora.get_threads(), desc
+
+
+def run_reference(args, wl):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import oracle as ora
+    shape = (1024, 1024) if len(wl["shape"]) == 2 else (96, 96, 96)
+    rho, u, T = make_fields(wl, shape)
+    s = ora.Oracle(wl["lattice"], wl["gamma"], wl["tau_f"], wl["tau_g"], shape)
+    s.init(rho, u, T)
+    N = int(np.prod(shape))
+    steps_per = 2
+    for _ in range(args.warmup):
+        s.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(steps_per)
+    dt = time.perf_counter() - t0
+    mlups = N * steps_per * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS (f+g)", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample": f"{'x'.join(map(str, shape))} box, {steps_per} steps per bench step"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": ora.get_threads(), "kind": "oracle",
+                         "sample": f"{'x'.join(map(str, shape))} periodic box of the same recipe, "
+                                   f"{steps_per} lattice steps per bench step"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, wl):
+    import torch
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(device)
+    from paper_1608_06345_gb300 import lbm
+    lbm.load()
+
+    prec = lbm.PREC_NAMES[wl["prec"]]
+    shape = wl["shape"]
+    D = len(shape)
+    N = int(np.prod(shape))
+    S = wl["steps"]
+    rho, u, T = make_fields(wl, shape)
+
+    stream = torch.cuda.current_stream()
+    solver = lbm.Solver(wl["lattice"], wl["gamma"], wl["tau_f"], wl["tau_g"], shape, prec=prec, stream=stream)
+    d_rho = torch.from_numpy(rho).to(device)
+    d_u = torch.from_numpy(np.ascontiguousarray(u)).to(device)
+    d_T = torch.from_numpy(T).to(device)
+    o_rho = torch.empty_like(d_rho)
+    o_u = torch.empty_like(d_u)
+    o_T = torch.empty_like(d_T)
+
+    def bench_step(ev_pairs=None):
+        solver.init(d_rho, d_u, d_T)
+        if ev_pairs is not None:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        solver.step(S)
+        if ev_pairs is not None:
+            b.record(stream)
+            ev_pairs.append((a, b))
+        solver.moments_device(o_rho, o_u, o_T)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 0)):
+        bench_step()
+    solver.sync()
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    step_events = []
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    barrier()
+    start.record(stream)
+    for _ in range(args.steps):
+        bench_step(step_events)
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    solver.sync()  # raises on a non-finite state
+    elapsed = start.elapsed_time(stop) / 1e3
+    step_kernel_s = sum(a.elapsed_time(b) for a, b in step_events) / 1e3 / (args.steps * S)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    updates = N * S * args.steps * world
+    mlups = updates / elapsed / 1e6
+
+    # end to end through the C ABI with host buffers: pinned fields in,
+    # moments out, copies inside the timed region
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h_rho, h_u, h_T = pin(rho), pin(u.reshape(-1)), pin(T)
+    r_rho = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    r_u = torch.empty(D * N, dtype=torch.float64).pin_memory().numpy()
+    r_T = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lbm.lbm_init(solver.h, h_rho, h_u, h_T)
+        lbm.lbm_step(solver.h, S)
+        lbm.lbm_moments(solver.h, r_rho, r_u, r_T)
+    barrier()
+    e2e_dt = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_dt], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    e2e_mlups = N * S * e2e_steps * world / e2e_dt / 1e6
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    word = {"f64": 8, "f32": 4, "f32_s16f": 2, "f32_s16bf": 2}[wl["prec"]]
+    Q = 37 if wl["lattice"] == 0 else 107
+    bytes_per_cell = 2 * Q * 2 * word
+    peak, peak_kind = measured_peaks()
+    achieved = N * bytes_per_cell / step_kernel_s / 1e9
+    key = f"k_step_{'d2q37' if wl['lattice'] == 0 else 'd3q107'}_{wl['prec']}_{'x'.join(map(str, shape))}"
+    traffic = recorded_traffic(key)
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, cores, desc = cpu_oracle_sample(wl, seconds_target=args.cpu_seconds)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": "MLUPS (f+g)", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl["prec"].split("_")[0], "data": "synthetic",
+        "config": {"workload": wl["desc"], "lattice": "D2Q37" if wl["lattice"] == 0 else "D3Q107",
+                   "grid": list(shape), "storage": wl["prec"], "lattice_steps_per_bench_step": S,
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2: state {2 * N * 2 * Q * word / 1e9:.1f} GB vs 0.13 GB L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": key, "bytes_per_cell_update": bytes_per_cell,
+                     "step_kernel_us": step_kernel_s * 1e6, "peak_kind": peak_kind},
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": (2 + D) * N * 8,
+                "d2h_bytes_per_step": (2 + D) * N * 8,
+                "note": "per bench step = one solve through lbm_init (pinned host fields) + lbm_step + "
+                        "lbm_moments (pinned host outputs)"},
+        "gpu_launches": args.steps * (S + 2),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="periodic2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

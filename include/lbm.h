@@ -1,0 +1,148 @@
+/*
+ * lbm.h -- C ABI of the GB300 thermal lattice Boltzmann library.
+ *
+ * The library advances the double-distribution thermal lattice Boltzmann
+ * scheme of Hu, Zhang & Geng (arXiv 1608.06345) on one GPU: per time step,
+ * every cell pulls its 2Q populations g_i (mass/momentum, Eq. (13a)) and h_i
+ * (internal energy, Eq. (13b)) from its upwind neighbours, takes the moments
+ * of Eq. (14)/(15), evaluates the fourth-order Hermite equilibrium of Eq. (18)
+ * and relaxes both populations with the explicit BGK step of Eq. (16)/(17).
+ * Velocity sets: D2Q37 (Table I) and D3Q107 (Table II).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an lbm_status; on failure lbm_last_error() gives a
+ *    thread-local, human-readable message.  No call aborts the process.
+ *  - Cell index of (x, y, z) is x + nx*(y + ny*z).  Scalar fields hold N =
+ *    nx*ny*nz doubles; velocity fields are component-major, D*N doubles
+ *    (u_x of every cell, then u_y, then u_z).
+ *  - Host pointers are caller-owned and only read/written during the call.
+ *    Device pointers are caller-owned and must stay valid until the stream
+ *    work that uses them has completed.
+ *  - All GPU work of an instance is issued on the stream given at creation
+ *    (NULL = the legacy default stream).  Calls that return host results
+ *    synchronise that stream.
+ *  - Units are the non-dimensional units of the paper's Sec. II: p = rho T,
+ *    velocities in units of sqrt(R T0); lattice spacing 1, time step 1, so
+ *    that xi_i = r c_i with the integer c_i of Tables I/II (Sec. V maps step
+ *    n to t = n / (X r)).  tau_f, tau_g are relaxation times in time steps.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_instance* lbm_handle;
+
+enum lbm_status {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,     /* invalid argument (message says which) */
+  LBM_ENOMEM = 2,     /* device or host allocation failed, or caller buffer too small */
+  LBM_ECUDA = 3,      /* a CUDA runtime call failed */
+  LBM_ENONFINITE = 4, /* a step produced a non-finite density or temperature */
+  LBM_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  LBM_EBUSY = 6       /* a pool's memory budget is full */
+};
+
+enum lbm_lattice { LBM_D2Q37 = 0, LBM_D3Q107 = 1 };
+
+/* Boundary kind per axis (both ends of an axis share it).
+ * LBM_ZERO_GRADIENT is the "open" boundary of Sec. V: a pull from outside
+ * [0, n-1] reads the edge cell's stored populations. */
+enum lbm_bc { LBM_PERIODIC = 0, LBM_ZERO_GRADIENT = 1 };
+
+/* Compute / storage precision of the populations.
+ *  LBM_F64      FP64 arithmetic, FP64 storage.
+ *  LBM_F32      FP32 arithmetic, FP32 storage.
+ *  LBM_F32_S16F / LBM_F32_S16BF: FP32 arithmetic; populations stored in
+ *               FP16 / BF16 as relative deviations from the instance's
+ *               reference equilibrium (rho0, u = 0, T0). */
+enum lbm_prec { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_S16F = 2, LBM_F32_S16BF = 3 };
+
+typedef struct {
+  int nx, ny, nz;       /* cells per axis; nz = 1 for D2Q37 */
+  int bc[3];            /* lbm_bc per axis x, y, z */
+  int prec;             /* lbm_prec */
+  void* stream;         /* cudaStream_t for all work of the instance; NULL = default stream */
+  void* device_mem;     /* optional caller-owned device buffer of >= lbm_state_bytes()
+                           bytes, 256-byte aligned; NULL = the library allocates */
+  size_t device_bytes;  /* size of device_mem */
+  double rho0, T0;      /* reference state of the 16-bit storage (ignored otherwise);
+                           0 means 1.0 */
+} lbm_grid;
+
+/* Device bytes an instance needs: two copies of the 2Q population planes
+ * (double buffer) plus a small tail (error word, reduction partials).
+ * Returns 0 for invalid arguments. */
+size_t lbm_state_bytes(int lattice, const lbm_grid* grid);
+
+/* Create an instance.  gamma sets delta = 2/(gamma-1) - D (Eq. (3)); it must
+ * give delta >= 0, i.e. 1 < gamma <= (D+2)/D.  tau_f relaxes g, tau_g relaxes
+ * h (Eq. (16)/(17); the paper uses one tau); both must exceed 0.5.
+ * Errors: LBM_EINVAL (bad lattice, gamma, tau, dims, bc, prec, nz != 1 in 2D,
+ * more than 2^31-1 cells), LBM_ENOMEM (allocation or device_mem too small),
+ * LBM_ECUDA.  On success *out owns the instance until lbm_destroy. */
+int lbm_create(lbm_handle* out, int lattice, double gamma, double tau_f, double tau_g,
+               const lbm_grid* grid);
+
+/* Release an instance and any memory the library allocated for it.  NULL-safe. */
+int lbm_destroy(lbm_handle h);
+
+/* Set the state to the equilibrium of the given fields (host arrays):
+ * g_i = F_i(rho, u, T) of Eq. (18), h_i = (delta/2) T F_i.  Copies the
+ * fields to the device through the instance's idle buffer and synchronises. */
+int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T);
+
+/* As lbm_init with device arrays; asynchronous on the instance's stream. */
+int lbm_init_device(lbm_handle h, const double* rho, const double* u, const double* T);
+
+/* Advance n >= 0 time steps (pull-stream + BGK collide of g and h per step).
+ * Asynchronous on the instance's stream. */
+int lbm_step(lbm_handle h, long n);
+
+/* rho, u, T of the stored (post-collision) state, Eq. (14)/(15), into host
+ * arrays of N, D*N, N doubles.  Synchronises; returns LBM_ENONFINITE if any
+ * step since creation met a non-finite density or temperature. */
+int lbm_moments(lbm_handle h, double* rho, double* u, double* T);
+
+/* As lbm_moments into device arrays; asynchronous, no status check. */
+int lbm_moments_device(lbm_handle h, double* rho, double* u, double* T);
+
+/* Grid totals of the stored state in FP64: out[0] = mass = sum g,
+ * out[1..D] = momentum = sum xi g, out[D+1] = total energy
+ * = sum (xi^2/2 g + h) (Eq. (14)).  Deterministic (fixed reduction order).
+ * Synchronises; LBM_ENONFINITE as for lbm_moments. */
+int lbm_conserved(lbm_handle h, double* out);
+
+/* Synchronise the instance's stream and report LBM_ENONFINITE / LBM_ECUDA. */
+int lbm_sync(lbm_handle h);
+
+/* Time steps taken since the last init. */
+long lbm_steps_done(lbm_handle h);
+
+/* Copy the raw population planes of the current state (2Q planes of N
+ * values in the storage type, velocity order of lbm_lattice_table) to or
+ * from host memory of lbm_raw_state_bytes() bytes, for checkpoint/restore.
+ * Synchronous. */
+size_t lbm_raw_state_bytes(lbm_handle h);
+int lbm_get_state(lbm_handle h, void* host, size_t bytes);
+int lbm_set_state(lbm_handle h, const void* host, size_t bytes);
+
+/* The library's own refined velocity set (Tables I/II, weights refined in
+ * FP64 so that the isotropy conditions of degree <= 8 hold to round-off):
+ * *q = Q; c[Q*D] integer velocities (row-major), w[Q] weights, *r the
+ * scaling factor (xi_i = r c_i).  Any output pointer may be NULL. */
+int lbm_lattice_table(int lattice, int* q, int* c, double* w, double* r);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,467 @@
+// Device code of the fused pull-stream + BGK-collide step and its helpers.
+//
+// Per cell and time step (paper: Eq. (13)-(18), Tables I/II, Sec. V):
+//   a1 pull     g~_i(x) = g*_i(x - c_i), h~_i(x) = h*_i(x - c_i)
+//   a2 moments  rho = sum g~, rho u = sum xi g~, rho E = sum xi^2/2 g~ + sum h~,
+//               T = (2E - u^2) / (D + delta)
+//   a3 F_i      w_i rho [A0 + A1 s + A2 s^2 + s^3/6 + s^4/24], s = xi_i.u, the
+//               fourth-order Hermite equilibrium of Eq. (18) regrouped in
+//               powers of s; A0..A2 depend on the velocity group only, so a
+//               (c, -c) pair shares the even part and flips the odd part.
+//   a4 Fh_i     (delta/2) T F_i
+//   a5 relax    g* = g~ + (F - g~)/tau_f,  h* = h~ + (Fh - h~)/tau_g; store.
+//
+// Representation: every population is held as its deviation from a fixed
+// reference equilibrium of the instance, g_i = gref_i + dg_i with
+// gref_i = F_i(rho0, u = 0, T0) and h_i = href_i + dh_i with
+// href_i = (delta/2) T0 gref_i.  This is an exact change of variables (the
+// scheme is linear in g, h given the moments, and the reference totals are
+// known: sum gref = rho0, sum xi gref = 0, sum xi^2/2 gref = rho0 D T0 / 2,
+// sum href = rho0 delta T0 / 2).  Working on the small dg, dh keeps FP32 and
+// 16-bit storage from losing the momentum to cancellation in sum xi_i g_i.
+//
+// Storage: structure of arrays, plane p (0..Q-1 for g, Q..2Q-1 for h) of N
+// cells at offset p * ps elements, cell index x + nx*(y + ny*z).  FP64/FP32
+// planes hold dg, dh; 16-bit planes hold dg/gref and dh/hscale.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lattice.h"
+
+namespace lbm {
+
+constexpr int kPeriodic = 0;
+constexpr int kZeroGradient = 1;
+
+// ---------------------------------------------------------------------------
+// compile-time helpers
+// ---------------------------------------------------------------------------
+template <int N, int I = 0, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<N, I + 1>(f);
+  }
+}
+
+template <int LAT>
+struct Lat {
+  static constexpr int D = (LAT == 0) ? 2 : 3;
+  static constexpr int Q = (LAT == 0) ? 37 : 107;
+  static constexpr int G = (LAT == 0) ? 8 : 10;
+  __host__ __device__ static constexpr int cx(int i) { return (LAT == 0 ? kD2Q37 : kD3Q107).c[i][0]; }
+  __host__ __device__ static constexpr int cy(int i) { return (LAT == 0 ? kD2Q37 : kD3Q107).c[i][1]; }
+  __host__ __device__ static constexpr int cz(int i) { return (LAT == 0 ? kD2Q37 : kD3Q107).c[i][2]; }
+  __host__ __device__ static constexpr int grp(int i) { return (LAT == 0 ? kD2Q37 : kD3Q107).grp[i]; }
+  __host__ __device__ static constexpr int c2(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
+};
+
+// ---------------------------------------------------------------------------
+// per-instance constants, already converted to the compute type C on the host
+// (a double->float conversion runs on the FP64 pipe, which is slow on GB300)
+// ---------------------------------------------------------------------------
+template <class C>
+struct Args {
+  int n[3];          // nx, ny, nz
+  int bc[3];         // kPeriodic / kZeroGradient per axis
+  long long ps;      // plane stride in elements
+  C r;               // xi = r c
+  C half_r2;         // r^2 / 2
+  C Dd;              // D + delta
+  C inv_Dd;          // 1 / (D + delta)
+  C half_delta;      // delta / 2
+  C omega_f;         // 1 / tau_f
+  C omega_g;         // 1 / tau_g
+  C rho0, T0, t0;    // reference state; t0 = T0 - 1
+  C wg[10];          // group weights
+  C x2g[10];         // group |xi|^2
+  C gref[10];        // reference equilibrium per group, w rho0 A0(u = 0, t0)
+  C pref[10];        // A0(u = 0, t0) - 1 per group
+  // 16-bit storage codec: dg = gref * d, dh = hscale * e
+  C inv_gref[10], hscale[10], inv_hscale[10];
+  unsigned int* flag;  // error word: bit 0 = non-finite rho or T met
+};
+
+// ---------------------------------------------------------------------------
+// storage codec
+// ---------------------------------------------------------------------------
+template <class S>
+struct IsS16 : std::integral_constant<bool, std::is_same<S, __half>::value ||
+                                              std::is_same<S, __nv_bfloat16>::value> {};
+
+template <class S>
+__device__ __forceinline__ S ldg_s(const S* p) {
+  if constexpr (std::is_same<S, __half>::value) {
+    unsigned short v = __ldg(reinterpret_cast<const unsigned short*>(p));
+    return __ushort_as_half(v);
+  } else if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+    unsigned short v = __ldg(reinterpret_cast<const unsigned short*>(p));
+    return __ushort_as_bfloat16(v);
+  } else {
+    return __ldg(p);
+  }
+}
+
+template <class S>
+__device__ __forceinline__ float s16_to_f(S v) {
+  if constexpr (std::is_same<S, __half>::value) return __half2float(v);
+  else return __bfloat162float(v);
+}
+
+template <class S>
+__device__ __forceinline__ S f_to_s16(float v) {
+  if constexpr (std::is_same<S, __half>::value) return __float2half_rn(v);
+  else return __float2bfloat16_rn(v);
+}
+
+// decode a stored population of group g into its deviation (dg or dh);
+// IS_H selects the h codec
+template <class S, class C, bool IS_H>
+__device__ __forceinline__ C decode(S v, int g, const Args<C>& a) {
+  if constexpr (IsS16<S>::value) {
+    const C d = static_cast<C>(s16_to_f(v));
+    return IS_H ? a.hscale[g] * d : a.gref[g] * d;
+  } else {
+    return static_cast<C>(v);
+  }
+}
+
+template <class S, class C, bool IS_H>
+__device__ __forceinline__ S encode(C v, int g, const Args<C>& a) {
+  if constexpr (IsS16<S>::value) {
+    const C d = IS_H ? v * a.inv_hscale[g] : v * a.inv_gref[g];
+    return f_to_s16<S>(static_cast<float>(d));
+  } else {
+    return static_cast<S>(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// equilibrium deviations (Eq. (18), regrouped by powers of s per group)
+//
+// With u2 = |u|^2, t = T - 1, x2 = |xi|^2 of the group:
+//   F_i / (w rho) = A0 + A1 s + A2 s^2 + s^3/6 + s^4/24
+//   A0 = 1 + P,  P = -u2/2 + t (x2 - D)/2 + u2^2/8 + t (D + 2 - x2) u2 / 4
+//                    + t^2 [x2^2 - 2 (D + 2) x2 + D (D + 2)] / 8
+//   A1 = 1 - u2/2 + t (x2 - D - 2)/2
+//   A2 = 1/2 - u2/4 + t (x2 - D - 4)/4
+// and the deviation from gref = w rho0 (1 + pref):
+//   dF_i = w [drho (1 + P) + rho0 (P - pref)] + w rho [A1 s + A2 s^2 + ...]
+//   dFh_i = (delta/2) (T dF_i + dT gref_i)
+// emit(i, dF_i, dFh_i) is called for every velocity.
+// ---------------------------------------------------------------------------
+template <int LAT, class C, class Emit>
+__device__ __forceinline__ void equilibrium_dev(C drho, const C (&u)[3], C dT, const Args<C>& a, Emit&& emit) {
+  using L = Lat<LAT>;
+  constexpr C D = C(L::D);
+  const C rho = a.rho0 + drho;
+  const C T = a.T0 + dT;
+  const C t = a.t0 + dT;
+  const C u2 = u[0] * u[0] + u[1] * u[1] + (L::D == 3 ? u[2] * u[2] : C(0));
+  // P = pa + pb x2 + pc x2^2;  A1 = be0 + be1 x2;  A2 = ga0 + ga1 x2
+  const C pa = -C(0.5) * u2 - C(0.5) * D * t + C(0.125) * u2 * u2 + C(0.25) * (D + C(2)) * t * u2 +
+               C(0.125) * D * (D + C(2)) * t * t;
+  const C pb = C(0.5) * t - C(0.25) * t * u2 - C(0.25) * (D + C(2)) * t * t;
+  const C pc = C(0.125) * t * t;
+  const C be0 = C(1) - C(0.5) * u2 - C(0.5) * (D + C(2)) * t;
+  const C be1 = C(0.5) * t;
+  const C ga0 = C(0.5) - C(0.25) * u2 - C(0.25) * (D + C(4)) * t;
+  const C ga1 = C(0.25) * t;
+  C c0[L::G], c1[L::G], c2[L::G], c3[L::G], c4[L::G], hr[L::G];
+#pragma unroll
+  for (int g = 0; g < L::G; ++g) {
+    const C x2 = a.x2g[g];
+    const C P = fma(x2, fma(x2, pc, pb), pa);
+    const C W = a.wg[g] * rho;
+    c0[g] = a.wg[g] * fma(drho, C(1) + P, a.rho0 * (P - a.pref[g]));
+    c1[g] = W * fma(be1, x2, be0);
+    c2[g] = W * fma(ga1, x2, ga0);
+    c3[g] = W * C(1.0 / 6.0);
+    c4[g] = W * C(1.0 / 24.0);
+    hr[g] = dT * a.gref[g];
+  }
+  const C ur[3] = {a.r * u[0], a.r * u[1], L::D == 3 ? a.r * u[2] : C(0)};
+  const C hd = a.half_delta;
+  emit(std::integral_constant<int, 0>{}, c0[0], hd * fma(T, c0[0], hr[0]));
+  static_for<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (i % 2 == 1) {
+      constexpr int g = L::grp(i);
+      constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+      C s = C(0);
+      if constexpr (cx != 0) s = fma(C(cx), ur[0], s);
+      if constexpr (cy != 0) s = fma(C(cy), ur[1], s);
+      if constexpr (cz != 0) s = fma(C(cz), ur[2], s);
+      const C s2 = s * s;
+      const C e = fma(s2, fma(s2, c4[g], c2[g]), c0[g]);
+      const C o = s * fma(s2, c3[g], c1[g]);
+      const C fp = e + o, fm = e - o;
+      emit(std::integral_constant<int, i>{}, fp, hd * fma(T, fp, hr[g]));
+      emit(std::integral_constant<int, i + 1>{}, fm, hd * fma(T, fm, hr[g]));
+    }
+  });
+}
+
+// ---------------------------------------------------------------------------
+// source coordinate of a pull along one axis (|c| <= 3)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pull_coord(int p, int c, int n, int bc) {
+  int q = p - c;
+  if (bc == kPeriodic) {
+    // n >= 1 and |c| <= 3: at most three corrections
+    while (q < 0) q += n;
+    while (q >= n) q -= n;
+  } else {
+    q = q < 0 ? 0 : (q > n - 1 ? n - 1 : q);
+  }
+  return q;
+}
+
+// ---------------------------------------------------------------------------
+// moments of a cell from the deviations (Eq. (14), (15))
+//   drho = sum dg, rho = rho0 + drho, rho u = r sum c dg,
+//   rho E = rho0 (D + delta) T0 / 2 + dK + dH with dK = r^2/2 sum c^2 dg, dH = sum dh,
+//   T = (2E - u^2)/(D + delta) = T0 + dT,
+//   dT = [2 (dK + dH) - rho u^2 - (D + delta) T0 drho] / (rho (D + delta))
+// ---------------------------------------------------------------------------
+template <int LAT, class C, class GetG, class GetH>
+__device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args<C>& a, C& drho, C (&u)[3],
+                                            C& dT) {
+  using L = Lat<LAT>;
+  C m = C(0), jx = C(0), jy = C(0), jz = C(0), k2 = C(0), H = C(0);
+  static_for<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const C gi = getg(I);
+    m += gi;
+    if constexpr (L::cx(i) != 0) jx = fma(C(L::cx(i)), gi, jx);
+    if constexpr (L::cy(i) != 0) jy = fma(C(L::cy(i)), gi, jy);
+    if constexpr (L::cz(i) != 0) jz = fma(C(L::cz(i)), gi, jz);
+    if constexpr (L::c2(i) != 0) k2 = fma(C(L::c2(i)), gi, k2);
+    H += geth(I);
+  });
+  const C rho = a.rho0 + m;
+  const C inv = C(1) / rho;
+  drho = m;
+  u[0] = a.r * jx * inv;
+  u[1] = a.r * jy * inv;
+  u[2] = (L::D == 3) ? a.r * jz * inv : C(0);
+  const C u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const C dE2 = C(2) * fma(a.half_r2, k2, H);
+  dT = (dE2 - rho * u2 - a.Dd * a.T0 * m) * inv * a.inv_Dd;
+}
+
+// ---------------------------------------------------------------------------
+// the fused step
+//   STAGE 0: the 2Q pulled values live in registers (D2Q37)
+//   STAGE 1: they are staged in shared memory by 4/8-byte cp.async (D3Q107,
+//            FP32/FP64 storage): no registers held while the loads fly
+//   STAGE 2: staged in shared memory by plain loads (D3Q107, 16-bit storage)
+// Grid: x = blocks of BX cells along a row, y = row, z = plane.
+// ---------------------------------------------------------------------------
+template <int LAT, class S, class C, int STAGE, int BX>
+__global__ void __launch_bounds__(BX) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const int x = blockIdx.x * BX + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  if (x >= nx) return;
+  // source offsets for lattice components c = -3..3 (index c + 3)
+  unsigned xo[7], yo[7], zo[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    xo[k] = (unsigned)pull_coord(x, k - 3, nx, a.bc[0]);
+    yo[k] = (unsigned)pull_coord(y, k - 3, ny, a.bc[1]) * (unsigned)nx;
+    zo[k] = (L::D == 3) ? (unsigned)pull_coord(z, k - 3, nz, a.bc[2]) * (unsigned)nx * (unsigned)ny : 0u;
+  }
+  const unsigned cell = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+  const long long ps = a.ps;
+  auto src_off = [&](auto I) -> unsigned {
+    constexpr int i = decltype(I)::value;
+    return zo[L::cz(i) + 3] + yo[L::cy(i) + 3] + xo[L::cx(i) + 3];
+  };
+
+  if constexpr (STAGE == 0) {
+    C g[Q], h[Q];
+    static_for<Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const unsigned off = src_off(I);
+      g[i] = decode<S, C, false>(ldg_s(src + i * ps + off), L::grp(i), a);
+      h[i] = decode<S, C, true>(ldg_s(src + (Q + i) * ps + off), L::grp(i), a);
+    });
+    C drho, u[3], dT;
+    moments_dev<LAT, C>([&](auto I) { return g[decltype(I)::value]; },
+                        [&](auto I) { return h[decltype(I)::value]; }, a, drho, u, dT);
+    if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+    equilibrium_dev<LAT, C>(drho, u, dT, a, [&](auto I, C dF, C dFh) {
+      constexpr int i = decltype(I)::value;
+      const C gn = fma(a.omega_f, dF - g[i], g[i]);
+      const C hn = fma(a.omega_g, dFh - h[i], h[i]);
+      dst[i * ps + cell] = encode<S, C, false>(gn, L::grp(i), a);
+      dst[(Q + i) * ps + cell] = encode<S, C, true>(hn, L::grp(i), a);
+    });
+  } else {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* sg = reinterpret_cast<S*>(smem_raw);  // [2Q][BX]
+    const int t = threadIdx.x;
+    static_for<Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const unsigned off = src_off(I);
+      if constexpr (STAGE == 1) {
+        static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
+        const unsigned sa0 = (unsigned)__cvta_generic_to_shared(sg + i * BX + t);
+        const unsigned sa1 = (unsigned)__cvta_generic_to_shared(sg + (Q + i) * BX + t);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa0), "l"(src + i * ps + off),
+                     "n"(sizeof(S)));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa1), "l"(src + (Q + i) * ps + off),
+                     "n"(sizeof(S)));
+      } else {
+        sg[i * BX + t] = ldg_s(src + i * ps + off);
+        sg[(Q + i) * BX + t] = ldg_s(src + (Q + i) * ps + off);
+      }
+    });
+    if constexpr (STAGE == 1) asm volatile("cp.async.wait_all;\n" ::: "memory");
+    // each thread reads back only the slots it filled itself
+    auto getg = [&](auto I) {
+      constexpr int i = decltype(I)::value;
+      return decode<S, C, false>(sg[i * BX + t], L::grp(i), a);
+    };
+    auto geth = [&](auto I) {
+      constexpr int i = decltype(I)::value;
+      return decode<S, C, true>(sg[(Q + i) * BX + t], L::grp(i), a);
+    };
+    C drho, u[3], dT;
+    moments_dev<LAT, C>(getg, geth, a, drho, u, dT);
+    if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+    equilibrium_dev<LAT, C>(drho, u, dT, a, [&](auto I, C dF, C dFh) {
+      constexpr int i = decltype(I)::value;
+      const C gi = getg(I), hi = geth(I);
+      const C gn = fma(a.omega_f, dF - gi, gi);
+      const C hn = fma(a.omega_g, dFh - hi, hi);
+      dst[i * ps + cell] = encode<S, C, false>(gn, L::grp(i), a);
+      dst[(Q + i) * ps + cell] = encode<S, C, true>(hn, L::grp(i), a);
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// init: g = F(rho, u, T), h = (delta/2) T F from FP64 device fields, stored
+// as deviations from the reference equilibrium (computed in FP64)
+// ---------------------------------------------------------------------------
+template <int LAT, class S>
+__global__ void k_init(S* __restrict__ dst, const double* __restrict__ rho, const double* __restrict__ u,
+                       const double* __restrict__ T, long long N, const Args<double> a,
+                       const Args<float> af) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+  const double drho = rho[cell] - a.rho0, dT = T[cell] - a.T0;
+  const double uu[3] = {u[cell], u[N + cell], L::D == 3 ? u[2 * N + cell] : 0.0};
+  const long long ps = a.ps;
+  equilibrium_dev<LAT, double>(drho, uu, dT, a, [&](auto I, double dF, double dFh) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (IsS16<S>::value) {
+      dst[i * ps + cell] = encode<S, float, false>(static_cast<float>(dF), L::grp(i), af);
+      dst[(Q + i) * ps + cell] = encode<S, float, true>(static_cast<float>(dFh), L::grp(i), af);
+    } else {
+      dst[i * ps + cell] = static_cast<S>(dF);
+      dst[(Q + i) * ps + cell] = static_cast<S>(dFh);
+    }
+  });
+}
+
+// decode a stored value to double (16-bit codec evaluated in FP32, as the step does)
+template <class S, bool IS_H>
+__device__ __forceinline__ double decode_d(S v, int g, const Args<float>& af) {
+  if constexpr (IsS16<S>::value) return static_cast<double>(decode<S, float, IS_H>(v, g, af));
+  else return static_cast<double>(v);
+}
+
+// ---------------------------------------------------------------------------
+// moments of the stored state, in FP64
+// ---------------------------------------------------------------------------
+template <int LAT, class S>
+__global__ void k_moments(const S* __restrict__ src, double* __restrict__ rho, double* __restrict__ u,
+                          double* __restrict__ T, long long N, const Args<double> a, const Args<float> af) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+  const long long ps = a.ps;
+  double drho, uu[3], dT;
+  moments_dev<LAT, double>(
+      [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        return decode_d<S, false>(src[i * ps + cell], L::grp(i), af);
+      },
+      [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        return decode_d<S, true>(src[(Q + i) * ps + cell], L::grp(i), af);
+      },
+      a, drho, uu, dT);
+  rho[cell] = a.rho0 + drho;
+  u[cell] = uu[0];
+  u[N + cell] = uu[1];
+  if (L::D == 3) u[2 * N + cell] = uu[2];
+  T[cell] = a.T0 + dT;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 conservation sums of the deviations: per-block partials, then one
+// fixed-order final pass; the host adds the reference totals N rho0 (mass)
+// and N rho0 (D + delta) T0 / 2 (energy)
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kRedMaxBlocks = 1024;
+constexpr int kRedVals = 5;  // mass, momentum[3], energy
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int LAT, class S>
+__global__ void __launch_bounds__(kRedThreads) k_conserve_partial(const S* __restrict__ src, long long N,
+                                                                   const Args<double> a, const Args<float> af,
+                                                                   double* __restrict__ partial) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const long long ps = a.ps;
+  double acc[kRedVals] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < N;
+       cell += (long long)gridDim.x * blockDim.x) {
+    static_for<Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const double gi = decode_d<S, false>(src[i * ps + cell], L::grp(i), af);
+      const double hi = decode_d<S, true>(src[(Q + i) * ps + cell], L::grp(i), af);
+      acc[0] += gi;
+      if constexpr (L::cx(i) != 0) acc[1] += (a.r * L::cx(i)) * gi;
+      if constexpr (L::cy(i) != 0) acc[2] += (a.r * L::cy(i)) * gi;
+      if constexpr (L::cz(i) != 0) acc[3] += (a.r * L::cz(i)) * gi;
+      acc[4] += a.half_r2 * L::c2(i) * gi + hi;
+    });
+  }
+  __shared__ double sh[kRedThreads / 32][kRedVals];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kRedVals; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) sh[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRedVals) {
+    double s = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) s += sh[w][threadIdx.x];
+    partial[blockIdx.x * kRedVals + threadIdx.x] = s;
+  }
+}
+
+
+}  // namespace lbm

@@ -1,0 +1,141 @@
+// Host FP64 lattice table: refined weights and scaling factor of the
+// D2Q37 (Table I) and D3Q107 (Table II) Hermite quadratures.
+//
+// The tables print r and the weights to 9-10 digits, which leaves the mass
+// moment off by 1e-8 and would make FP64 runs drift.  The table is therefore
+// recomputed from its defining property: the weighted velocity moments
+// sum_i w_i xi_i^alpha must equal those of the unit Gaussian for the
+// even-moment classes of degree 0..8 (G+1 conditions for G weights and r).
+//
+// Method: for a fixed r the conditions are linear in the group weights.
+// All conditions but x^8 determine w(r) by a dense solve; r is then the root
+// of the remaining x^8 condition, found by the secant method from [1.19, 1.20]
+// (the printed r is 1.19697977).
+#include <cmath>
+#include <cstring>
+
+#include "lattice.h"
+
+namespace lbm {
+namespace {
+
+double gaussian_moment(int n) {  // (n-1)!! for even n
+  if (n % 2) return 0.0;
+  double m = 1.0;
+  for (int k = n - 1; k > 1; k -= 2) m *= k;
+  return m;
+}
+
+// Dense LU solve with partial pivoting; returns false if singular.
+bool lu_solve(int n, double* a, double* b) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(a[i * n + k]) > std::fabs(a[p * n + k])) p = i;
+    if (a[p * n + k] == 0.0) return false;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(a[k * n + j], a[p * n + j]);
+      std::swap(b[k], b[p]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double l = a[i * n + k] / a[k * n + k];
+      a[i * n + k] = 0.0;
+      for (int j = k + 1; j < n; ++j) a[i * n + j] -= l * a[k * n + j];
+      b[i] -= l * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= a[i * n + j] * b[j];
+    b[i] = s / a[i * n + i];
+  }
+  return true;
+}
+
+struct Problem {
+  const LatticeDef* L;
+  int nlin;              // conditions solved linearly (= G)
+  int mono[11][3];       // exponents; mono[nlin] is the secant condition x^8
+};
+
+// sum over the members of group g of (r c)^alpha
+double group_moment(const LatticeDef& L, int g, const int* alpha, double r) {
+  double s = 0.0;
+  for (int i = 0; i < L.Q; ++i) {
+    if (L.grp[i] != g) continue;
+    double m = 1.0;
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < alpha[a]; ++k) m *= r * L.c[i][a];
+    s += m;
+  }
+  return s;
+}
+
+double target(const int* alpha) {
+  return gaussian_moment(alpha[0]) * gaussian_moment(alpha[1]) * gaussian_moment(alpha[2]);
+}
+
+// Weights for a given r (linear conditions); returns the x^8 residual.
+bool weights_for(const Problem& P, double r, double* w, double* resid) {
+  const LatticeDef& L = *P.L;
+  const int n = P.nlin;
+  double a[100], b[10];
+  for (int k = 0; k < n; ++k) {
+    for (int g = 0; g < n; ++g) a[k * n + g] = group_moment(L, g, P.mono[k], r);
+    b[k] = target(P.mono[k]);
+  }
+  if (!lu_solve(n, a, b)) return false;
+  double s = 0.0;
+  for (int g = 0; g < n; ++g) {
+    w[g] = b[g];
+    s += w[g] * group_moment(L, g, P.mono[n], r);
+  }
+  *resid = s - target(P.mono[n]);
+  return true;
+}
+
+}  // namespace
+
+int build_lattice_table(int lattice, LatticeTable* out) {
+  Problem P{};
+  if (lattice == 0) {
+    static const int m[9][3] = {{0, 0, 0}, {2, 0, 0}, {4, 0, 0}, {2, 2, 0}, {6, 0, 0},
+                                {4, 2, 0}, {6, 2, 0}, {4, 4, 0}, {8, 0, 0}};
+    P.L = &kD2Q37;
+    P.nlin = 8;
+    std::memcpy(P.mono, m, sizeof(m));
+  } else if (lattice == 1) {
+    static const int m[11][3] = {{0, 0, 0}, {2, 0, 0}, {4, 0, 0}, {2, 2, 0}, {6, 0, 0}, {4, 2, 0},
+                                 {2, 2, 2}, {6, 2, 0}, {4, 4, 0}, {4, 2, 2}, {8, 0, 0}};
+    P.L = &kD3Q107;
+    P.nlin = 10;
+    std::memcpy(P.mono, m, sizeof(m));
+  } else {
+    return -1;
+  }
+  double w[10];
+  double r0 = 1.19, r1 = 1.20, f0, f1;
+  if (!weights_for(P, r0, w, &f0) || !weights_for(P, r1, w, &f1)) return -2;
+  for (int it = 0; it < 100 && f1 != f0; ++it) {
+    double r2 = r1 - f1 * (r1 - r0) / (f1 - f0);
+    r0 = r1;
+    f0 = f1;
+    r1 = r2;
+    if (!weights_for(P, r1, w, &f1)) return -2;
+    if (std::fabs(r1 - r0) <= 1e-16 * r1) break;
+  }
+  if (!weights_for(P, r1, w, &f1)) return -2;
+  const LatticeDef& L = *P.L;
+  out->D = L.D;
+  out->Q = L.Q;
+  out->G = L.G;
+  out->r = r1;
+  for (int g = 0; g < L.G; ++g) {
+    out->wg[g] = w[g];
+    out->x2g[g] = r1 * r1 * L.c2[g];
+  }
+  for (int g = L.G; g < 10; ++g) out->wg[g] = out->x2g[g] = 0.0;
+  return 0;
+}
+
+}  // namespace lbm

@@ -1,0 +1,80 @@
+// Launcher templates: pick the step shape, set up and launch the kernels of
+// one (lattice, storage type, compute type).
+#pragma once
+
+#include "runtime.h"
+
+namespace lbm {
+
+template <int LAT, class S, class C, int STAGE, int BX>
+cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, const Args<C>& a) {
+  const dim3 grid((unsigned)((inst->n[0] + BX - 1) / BX), (unsigned)inst->n[1], (unsigned)inst->n[2]);
+  size_t smem = 0;
+  if constexpr (STAGE != 0) {
+    smem = sizeof(S) * 2 * Lat<LAT>::Q * BX;
+    // the shared-memory opt-in is a per-device function attribute: set it
+    // once per device (bit d of the mask) for this template instance
+    static unsigned long long configured = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(configured & (1ull << dev))) {
+      e = cudaFuncSetAttribute(k_step<LAT, S, C, STAGE, BX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      if (dev < 64) configured |= (1ull << dev);
+    }
+  }
+  k_step<LAT, S, C, STAGE, BX><<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst),
+                                                                  a);
+  return cudaGetLastError();
+}
+
+template <int LAT, class S, class C>
+cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst) {
+  const StepShape& sh = inst->shape;
+  const Args<C>* ap;
+  if constexpr (std::is_same<C, double>::value) ap = &inst->ad;
+  else ap = &inst->af;
+  const Args<C>& a = *ap;
+  if constexpr (LAT == 0) {
+    if (sh.bx == 256) return launch_step_t<LAT, S, C, 0, 256>(inst, src, dst, a);
+    return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a);
+  } else if constexpr (sizeof(S) >= 4) {
+    return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a);
+  } else {
+    return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a);
+  }
+}
+
+inline unsigned blocks_for(long long N, int t) { return (unsigned)((N + t - 1) / t); }
+
+template <int LAT, class S>
+cudaError_t launch_init_t(const Instance* inst, void* dst, const double* rho, const double* u, const double* T) {
+  constexpr int kT = 128;
+  if (inst->N == 0) return cudaSuccess;
+  k_init<LAT, S><<<blocks_for(inst->N, kT), kT, 0, inst->stream>>>(static_cast<S*>(dst), rho, u, T, inst->N,
+                                                                   inst->ad, inst->af);
+  return cudaGetLastError();
+}
+
+
+template <int LAT, class S>
+cudaError_t launch_moments_t(const Instance* inst, const void* src, double* rho, double* u, double* T) {
+  constexpr int kT = 128;
+  if (inst->N == 0) return cudaSuccess;
+  k_moments<LAT, S><<<blocks_for(inst->N, kT), kT, 0, inst->stream>>>(static_cast<const S*>(src), rho, u, T,
+                                                                      inst->N, inst->ad, inst->af);
+  return cudaGetLastError();
+}
+
+
+template <int LAT, class S>
+cudaError_t launch_conserve_t(const Instance* inst, const void* src, double* partial, int nblocks) {
+  k_conserve_partial<LAT, S><<<nblocks, kRedThreads, 0, inst->stream>>>(static_cast<const S*>(src), inst->N,
+                                                                         inst->ad, inst->af, partial);
+  return cudaGetLastError();
+}
+
+
+}  // namespace lbm

@@ -1,0 +1,66 @@
+// Internal runtime of the library: the instance record and the launchers
+// that each lattice's translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "lattice.h"
+
+namespace lbm {
+
+enum Prec { kF64 = 0, kF32 = 1, kF32S16F = 2, kF32S16BF = 3 };
+
+// Kernel launch shape of the step, per (lattice, precision); chosen by the
+// built-in defaults or the autotuner.
+struct StepShape {
+  int bx;     // cells per block along x
+  int stage;  // 0 registers, 1 cp.async shared staging, 2 plain shared staging
+};
+
+struct Instance {
+  int lattice, prec, D, Q, G;
+  int n[3], bc[3];
+  long long N;         // cells
+  long long ps;        // plane stride (elements), N rounded up to 64
+  size_t word;         // bytes per stored population
+  size_t buf_bytes;    // bytes of one population buffer (2Q planes)
+  cudaStream_t stream;
+  unsigned char* mem;  // base of the device allocation
+  bool own_mem;
+  void* buf[2];        // population buffers
+  int cur;             // buffer holding the current state
+  unsigned int* flag;  // device error word
+  double* red_out;     // device: final conservation sums (kRedVals)
+  double* red_partial; // device: per-block partials (kRedMaxBlocks * kRedVals)
+  LatticeTable table;
+  double gamma, delta, tau_f, tau_g, rho0, T0;
+  long steps_done;
+  Args<double> ad;
+  Args<float> af;
+  StepShape shape;
+};
+
+// Bytes of the tail region after the two buffers.
+constexpr size_t kTailBytes = 256 /*flag*/ + 256 /*red_out*/ + sizeof(double) * kRedMaxBlocks * kRedVals;
+
+inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Launchers of one (lattice, precision) pair; each pair is compiled as its
+// own object from step_inst.cu.  All launch on inst->stream and return the
+// CUDA error of the launch.
+struct Launchers {
+  cudaError_t (*step)(const Instance* inst, const void* src, void* dst);
+  cudaError_t (*init)(const Instance* inst, void* dst, const double* rho, const double* u, const double* T);
+  cudaError_t (*moments)(const Instance* inst, const void* src, double* rho, double* u, double* T);
+  cudaError_t (*conserve)(const Instance* inst, const void* src, double* partial, int nblocks);
+};
+
+extern const Launchers kLaunchers_0_0, kLaunchers_0_1, kLaunchers_0_2, kLaunchers_0_3;
+extern const Launchers kLaunchers_1_0, kLaunchers_1_1, kLaunchers_1_2, kLaunchers_1_3;
+
+StepShape default_shape(int lattice, int prec);
+
+}  // namespace lbm

@@ -1,0 +1,40 @@
+// Kernel instantiations and launchers of one (lattice, precision) pair,
+// selected at compile time by LBM_LAT (0 = D2Q37, 1 = D3Q107) and LBM_PREC
+// (0 = FP64, 1 = FP32, 2 = FP32 compute / FP16 storage, 3 = FP32 / BF16).
+// The build compiles this file once per pair so the objects build in parallel.
+#include "launch_impl.cuh"
+
+#ifndef LBM_LAT
+#error "LBM_LAT must be defined"
+#endif
+#ifndef LBM_PREC
+#error "LBM_PREC must be defined"
+#endif
+
+namespace lbm {
+
+#if LBM_PREC == 0
+using StoreT = double;
+using ComputeT = double;
+#elif LBM_PREC == 1
+using StoreT = float;
+using ComputeT = float;
+#elif LBM_PREC == 2
+using StoreT = __half;
+using ComputeT = float;
+#else
+using StoreT = __nv_bfloat16;
+using ComputeT = float;
+#endif
+
+#define LBM_CAT2(a, b, c) a##_##b##_##c
+#define LBM_CAT(a, b, c) LBM_CAT2(a, b, c)
+
+extern const Launchers LBM_CAT(kLaunchers, LBM_LAT, LBM_PREC) = {
+    &launch_step_shape<LBM_LAT, StoreT, ComputeT>,
+    &launch_init_t<LBM_LAT, StoreT>,
+    &launch_moments_t<LBM_LAT, StoreT>,
+    &launch_conserve_t<LBM_LAT, StoreT>,
+};
+
+}  // namespace lbm

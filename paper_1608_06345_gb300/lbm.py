@@ -1,0 +1,280 @@
+"""Python binding of the C ABI in ``include/lbm.h`` (ctypes).
+
+The functions keep the C names (``lbm_create``, ``lbm_init``, ``lbm_step``,
+``lbm_moments``, ``lbm_conserved``, ``lbm_destroy`` ...) and only marshal
+arguments; every step of the computation runs in the CUDA library.  PyTorch
+supplies device memory (``Solver`` allocates the instance's buffer as a torch
+tensor, so it comes from torch's caching allocator) and streams.
+
+There is no CPU fallback: if the shared library is missing the import fails
+loudly (build it with ``python -m paper_1608_06345_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EBUSY = range(7)
+LBM_D2Q37, LBM_D3Q107 = 0, 1
+LBM_PERIODIC, LBM_ZERO_GRADIENT = 0, 1
+LBM_F64, LBM_F32, LBM_F32_S16F, LBM_F32_S16BF = 0, 1, 2, 3
+
+PREC_NAMES = {"f64": LBM_F64, "f32": LBM_F32, "f32_s16f": LBM_F32_S16F, "f32_s16bf": LBM_F32_S16BF}
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
+                5: "LBM_ETIMEOUT", 6: "LBM_EBUSY"}
+
+# every entry point of include/lbm.h
+EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init_device", "lbm_step",
+           "lbm_moments", "lbm_moments_device", "lbm_conserved", "lbm_sync", "lbm_steps_done",
+           "lbm_raw_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_lattice_table", "lbm_last_error"]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lbm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("bc", ctypes.c_int * 3), ("prec", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("device_mem", ctypes.c_void_p), ("device_bytes", ctypes.c_size_t),
+                ("rho0", ctypes.c_double), ("T0", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load liblbm.so (raising if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError(f"CUDA library not built: {path} (run python -m paper_1608_06345_gb300.build)")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    gp = ctypes.POINTER(lbm_grid)
+    sig = {
+        "lbm_state_bytes": (ctypes.c_size_t, [ctypes.c_int, gp]),
+        "lbm_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, gp]),
+        "lbm_destroy": (ctypes.c_int, [vp]),
+        "lbm_init": (ctypes.c_int, [vp, vp, vp, vp]),
+        "lbm_init_device": (ctypes.c_int, [vp, vp, vp, vp]),
+        "lbm_step": (ctypes.c_int, [vp, ctypes.c_long]),
+        "lbm_moments": (ctypes.c_int, [vp, vp, vp, vp]),
+        "lbm_moments_device": (ctypes.c_int, [vp, vp, vp, vp]),
+        "lbm_conserved": (ctypes.c_int, [vp, dp]),
+        "lbm_sync": (ctypes.c_int, [vp]),
+        "lbm_steps_done": (ctypes.c_long, [vp]),
+        "lbm_raw_state_bytes": (ctypes.c_size_t, [vp]),
+        "lbm_get_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+        "lbm_set_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+        "lbm_lattice_table": (ctypes.c_int, [ctypes.c_int, ip, ip, dp, dp]),
+        "lbm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None for None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def dim(lattice):
+    return 2 if lattice == LBM_D2Q37 else 3
+
+
+def make_grid(shape, bc=(LBM_PERIODIC,) * 3, prec=LBM_F32, stream=None, device_mem=None, device_bytes=0,
+              rho0=0.0, T0=0.0):
+    shape = tuple(int(s) for s in shape) + (1,) * (3 - len(shape))
+    bc = tuple(bc) + (LBM_PERIODIC,) * (3 - len(bc))
+    g = lbm_grid()
+    g.nx, g.ny, g.nz = shape
+    g.bc[0], g.bc[1], g.bc[2] = bc[:3]
+    g.prec = prec
+    g.stream = stream
+    g.device_mem = device_mem
+    g.device_bytes = device_bytes
+    g.rho0 = rho0
+    g.T0 = T0
+    return g
+
+
+def lbm_state_bytes(lattice, grid):
+    return load().lbm_state_bytes(lattice, ctypes.byref(grid))
+
+
+def lbm_create(lattice, gamma, tau_f, tau_g, grid):
+    h = ctypes.c_void_p()
+    _check(load().lbm_create(ctypes.byref(h), lattice, gamma, tau_f, tau_g, ctypes.byref(grid)))
+    return h
+
+
+def lbm_destroy(h):
+    return _check(load().lbm_destroy(h))
+
+
+def lbm_init(h, rho, u, T):
+    return _check(load().lbm_init(h, _ptr(rho), _ptr(u), _ptr(T)))
+
+
+def lbm_init_device(h, rho, u, T):
+    return _check(load().lbm_init_device(h, _ptr(rho), _ptr(u), _ptr(T)))
+
+
+def lbm_step(h, n):
+    return _check(load().lbm_step(h, int(n)))
+
+
+def lbm_moments(h, rho, u, T):
+    return _check(load().lbm_moments(h, _ptr(rho), _ptr(u), _ptr(T)))
+
+
+def lbm_moments_device(h, rho, u, T):
+    return _check(load().lbm_moments_device(h, _ptr(rho), _ptr(u), _ptr(T)))
+
+
+def lbm_conserved(h, D):
+    out = np.zeros(2 + D)
+    _check(load().lbm_conserved(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def lbm_sync(h):
+    return _check(load().lbm_sync(h))
+
+
+def lbm_steps_done(h):
+    return load().lbm_steps_done(h)
+
+
+def lbm_raw_state_bytes(h):
+    return load().lbm_raw_state_bytes(h)
+
+
+def lbm_get_state(h, host):
+    return _check(load().lbm_get_state(h, _ptr(host), host.nbytes))
+
+
+def lbm_set_state(h, host):
+    return _check(load().lbm_set_state(h, _ptr(host), host.nbytes))
+
+
+def lbm_lattice_table(lattice):
+    """(c[Q, D], w[Q], r) of the library's refined lattice."""
+    q = ctypes.c_int()
+    D = dim(lattice)
+    c = np.zeros(107 * D, dtype=np.int32)
+    w = np.zeros(107)
+    r = ctypes.c_double()
+    _check(load().lbm_lattice_table(lattice, ctypes.byref(q), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                    w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(r)))
+    Q = q.value
+    return c[: Q * D].reshape(Q, D).astype(np.int64), w[:Q].copy(), r.value
+
+
+def lbm_last_error():
+    return load().lbm_last_error().decode()
+
+
+class Solver:
+    """One simulation instance on the current CUDA device.
+
+    Device memory is a torch uint8 tensor of ``lbm_state_bytes`` (torch's
+    caching allocator); work runs on ``stream`` (default: torch's current
+    stream), so torch events and syncs order correctly with it."""
+
+    def __init__(self, lattice, gamma, tau_f, tau_g, shape, bc=(LBM_PERIODIC,) * 3, prec=LBM_F32,
+                 stream=None, rho0=0.0, T0=0.0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Solver needs a CUDA device")
+        self.lattice = lattice
+        self.D = dim(lattice)
+        self.Q = 37 if lattice == LBM_D2Q37 else 107
+        shape = tuple(int(s) for s in shape) + (1,) * (3 - len(shape))
+        self.shape = shape
+        self.N = shape[0] * shape[1] * shape[2]
+        self.prec = prec
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = make_grid(shape, bc, prec, stream=self.stream.cuda_stream, rho0=rho0, T0=T0)
+        nbytes = lbm_state_bytes(lattice, g)
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "invalid grid")
+        with torch.cuda.stream(self.stream):
+            self.mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        g.device_mem = self.mem.data_ptr()
+        g.device_bytes = nbytes
+        self.grid = g
+        self.h = lbm_create(lattice, gamma, tau_f, tau_g, g)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, rho, u, T):
+        """Host (numpy float64) or device (torch float64 cuda) fields."""
+        if isinstance(rho, np.ndarray):
+            rho = np.ascontiguousarray(rho, dtype=np.float64)
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            T = np.ascontiguousarray(T, dtype=np.float64)
+            assert rho.size == self.N and u.size == self.D * self.N and T.size == self.N
+            lbm_init(self.h, rho, u, T)
+        else:
+            assert rho.is_cuda and rho.is_contiguous() and u.is_contiguous() and T.is_contiguous()
+            lbm_init_device(self.h, rho, u, T)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def moments(self):
+        rho = np.zeros(self.N)
+        u = np.zeros(self.D * self.N)
+        T = np.zeros(self.N)
+        lbm_moments(self.h, rho, u, T)
+        return rho, u.reshape(self.D, self.N), T
+
+    def moments_device(self, rho, u, T):
+        lbm_moments_device(self.h, rho, u, T)
+
+    def conserved(self):
+        return lbm_conserved(self.h, self.D)
+
+    def sync(self):
+        lbm_sync(self.h)

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs, element by element on rho, u, T.
+
+Tolerances: FP64 <= 1e-12, FP32 <= 1e-5 (relative, parity norm of
+tests/parity.py) on well-conditioned flows (random and Fourier-mode fields,
+the paper's own shock tube in FP64).  The classic Sod tube amplifies
+round-off by 10^3-10^5 over a few hundred steps (the oracle itself moves by
+more than 1e-12 when its inputs move by 4 ulps), so there the tolerance is
+derived from that measured sensitivity (tests/parity.py).  Sizes span several
+thread blocks with a ragged tail (D2Q37 blocks are 128 cells along x, D3Q107
+blocks 64), Ny and Nz below the stencil width 7, and both boundary kinds."""
+import numpy as np
+import pytest
+
+import lbm_inputs as li
+from oracle import oracle as ora
+from tests.parity import TOL, assert_parity, conditioned_tolerance, run_gpu, run_oracle, sensitivity
+
+pytestmark = pytest.mark.gpu
+
+P, ZG = ora.PERIODIC, ora.ZERO_GRADIENT
+F64, F32 = 0, 1
+
+
+def fields_for(shape, seed):
+    D = len(shape)
+    N = int(np.prod(shape))
+    return li.random_fields(N, D, seed=seed)
+
+
+CASES_2D = [
+    # shape, bc, gamma, tau_f, tau_g, steps
+    ((300, 7), (P, P), 1.4, 0.6, 0.6, 40),
+    ((37, 4), (P, P), 1.4, 0.55, 0.7, 60),
+    ((131, 5), (ZG, P), 1.3, 0.8, 0.65, 50),
+    ((64, 1), (P, P), 1.1, 0.6, 0.6, 30),
+    ((5, 9), (ZG, ZG), 5.0 / 3.0, 0.9, 0.9, 20),
+    ((1, 1), (P, P), 1.4, 0.6, 0.6, 5),
+]
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("case", CASES_2D)
+def test_d2q37_random_fields(case, prec):
+    shape, bc, gamma, tf, tg, steps = case
+    fields = fields_for(shape, seed=sum(shape) + steps)
+    ref, _ = run_oracle(ora.D2Q37, gamma, tf, tg, shape, bc, fields, steps)
+    gpu, _ = run_gpu(0, gamma, tf, tg, shape, bc, fields, steps, prec)
+    assert_parity(gpu, ref, gamma, TOL["f64" if prec == F64 else "f32"])
+
+
+CASES_3D = [
+    ((150, 5, 6), (P, P, P), 1.4, 0.6, 0.6, 12),
+    ((20, 3, 4), (ZG, P, P), 1.3, 0.7, 0.8, 15),
+    ((9, 7, 5), (P, ZG, ZG), 5.0 / 3.0, 0.6, 0.6, 10),
+]
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("case", CASES_3D)
+def test_d3q107_random_fields(case, prec):
+    shape, bc, gamma, tf, tg, steps = case
+    fields = fields_for(shape, seed=sum(shape) + steps)
+    ref, _ = run_oracle(ora.D3Q107, gamma, tf, tg, shape, bc, fields, steps)
+    gpu, _ = run_gpu(1, gamma, tf, tg, shape, bc, fields, steps, prec)
+    assert_parity(gpu, ref, gamma, TOL["f64" if prec == F64 else "f32"])
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("steps", [180, 500])
+def test_sod_tube_1000x4(steps, prec):
+    """Classic Sod on 1000 x 4 (periodic y, zero-gradient x), gamma 1.4,
+    tau_f = tau_g = 0.6.  This flow amplifies round-off (the shock leaves
+    through the open end near step 340 and the state drifts from the exact
+    one), so the tolerance is derived from the oracle's own sensitivity to
+    round-off of the tested precision (tests/parity.py); the conserved totals
+    must agree as well."""
+    shape, bc = (1000, 4), (ZG, P)
+    fields = li.sod_fields(1000, 4)
+    ref, cref = run_oracle(ora.D2Q37, 1.4, 0.6, 0.6, shape, bc, fields, steps)
+    kappa = sensitivity(ora.D2Q37, 1.4, 0.6, 0.6, shape, bc, fields, steps, prec, ref=ref)
+    gpu, cgpu = run_gpu(0, 1.4, 0.6, 0.6, shape, bc, fields, steps, prec)
+    tol = conditioned_tolerance(prec, kappa, steps)
+    assert_parity(gpu, ref, 1.4, tol)
+    rtol = 1e-12 if prec == F64 else 1e-6
+    np.testing.assert_allclose(cgpu, cref, rtol=rtol, atol=rtol * abs(cref[0]))
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_sod_tube_3d_1024x4x4(prec):
+    """Classic Sod on the D3Q107 lattice, 1024 x 4 x 4, 100 steps; tolerance
+    derived from the oracle's sensitivity as for the 2D tube."""
+    shape, bc = (1024, 4, 4), (ZG, P, P)
+    fields = li.sod_fields(1024, 4, 4, D=3)
+    ref, _ = run_oracle(ora.D3Q107, 1.4, 0.6, 0.6, shape, bc, fields, 100)
+    kappa = sensitivity(ora.D3Q107, 1.4, 0.6, 0.6, shape, bc, fields, 100, prec, ref=ref)
+    gpu, _ = run_gpu(1, 1.4, 0.6, 0.6, shape, bc, fields, 100, prec)
+    assert_parity(gpu, ref, 1.4, conditioned_tolerance(prec, kappa, 100))
+
+
+@pytest.mark.parametrize("steps", [180, 500])
+def test_paper_shock_tube_2d_fp64(steps):
+    """The paper's own 2D case (Sec. V): D2Q37, 1000 x 16, delta = 3,
+    tau = 2/3, rho 4|1, T 1|1; FP64 within 1e-12 of the oracle."""
+    shape, bc = (1000, 16), (ZG, P)
+    fields = li.sod_fields(1000, 16, left=(4.0, 0.0, 1.0), right=(1.0, 0.0, 1.0))
+    ref, _ = run_oracle(ora.D2Q37, 1.4, 2 / 3, 2 / 3, shape, bc, fields, steps)
+    gpu, _ = run_gpu(0, 1.4, 2 / 3, 2 / 3, shape, bc, fields, steps, F64)
+    assert_parity(gpu, ref, 1.4, 1e-12)
+
+
+def test_paper_shock_tube_fp32():
+    """The paper's 2D tube in FP32: the shock position moves with round-off,
+    so the bar is the conditioned tolerance."""
+    shape, bc = (1000, 16), (ZG, P)
+    fields = li.sod_fields(1000, 16, left=(4.0, 0.0, 1.0), right=(1.0, 0.0, 1.0))
+    ref, _ = run_oracle(ora.D2Q37, 1.4, 2 / 3, 2 / 3, shape, bc, fields, 180)
+    kappa = sensitivity(ora.D2Q37, 1.4, 2 / 3, 2 / 3, shape, bc, fields, 180, F32, ref=ref)
+    gpu, _ = run_gpu(0, 1.4, 2 / 3, 2 / 3, shape, bc, fields, 180, F32)
+    assert_parity(gpu, ref, 1.4, conditioned_tolerance(F32, kappa, 180))
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_periodic_fourier_box_512(prec):
+    """The periodic-box recipe (8 random Fourier modes, u amplitude 0.02,
+    1% density) at 512^2, gamma 1.4, tau_f 0.55, tau_g 0.7, 200 steps: a
+    smooth, well-conditioned flow, held to the plain bars 1e-12 / 1e-5."""
+    shape = (512, 512)
+    fields = li.fourier_fields(shape, seed_u=1, seed_rho=2)
+    ref, _ = run_oracle(ora.D2Q37, 1.4, 0.55, 0.7, shape, (P, P), fields, 200)
+    gpu, _ = run_gpu(0, 1.4, 0.55, 0.7, shape, (P, P), fields, 200, prec)
+    assert_parity(gpu, ref, 1.4, TOL["f64" if prec == F64 else "f32"])
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_periodic_fourier_box_3d(prec):
+    """The 3D periodic recipe (rho, u, T modes, k in [-4, 4]) at 48^3,
+    gamma 1.3 (delta = 11/3, non-integer), tau 0.6, 40 steps."""
+    shape = (48, 48, 48)
+    fields = li.fourier_fields(shape, seed_u=3, seed_rho=4, seed_T=5)
+    ref, _ = run_oracle(ora.D3Q107, 1.3, 0.6, 0.6, shape, (P, P, P), fields, 40)
+    gpu, _ = run_gpu(1, 1.3, 0.6, 0.6, shape, (P, P, P), fields, 40, prec)
+    assert_parity(gpu, ref, 1.3, TOL["f64" if prec == F64 else "f32"])
+
+
+@pytest.mark.parametrize("lat,shape", [(0, (48, 40)), (1, (12, 10, 8))])
+def test_conserved_totals_match_oracle_and_are_conserved(lat, shape):
+    D = len(shape)
+    fields = fields_for(shape, seed=77)
+    _, c0 = run_oracle(lat, 1.4, 0.6, 0.6, shape, (P,) * D, fields, 0)
+    ref, cref = run_oracle(lat, 1.4, 0.6, 0.6, shape, (P,) * D, fields, 25)
+    gpu, cgpu = run_gpu(lat, 1.4, 0.6, 0.6, shape, (P,) * D, fields, 25, F64)
+    scale = np.array([c0[0]] * (1 + D) + [c0[-1]])
+    assert np.all(np.abs(cgpu - cref) / scale < 1e-13)
+    assert np.all(np.abs(cgpu - c0) / scale < 1e-13)
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_uniform_state_stays_uniform(prec):
+    from paper_1608_06345_gb300 import lbm
+    shape = (77, 6)
+    N = 77 * 6
+    fields = li.uniform_fields(N, 2, rho=1.2, u=[0.05, -0.02], T=0.95)
+    s = lbm.Solver(0, 1.4, 0.7, 0.7, shape, bc=(ZG, P), prec=prec)
+    s.init(*fields)
+    s.step(30)
+    rho, u, T = s.moments()
+    for q in (rho, u[0], u[1], T):
+        assert np.ptp(q) == 0.0
+    tol = 1e-14 if prec == F64 else 2e-6
+    assert abs(rho[0] - 1.2) < tol and abs(T[0] - 0.95) < tol
+
+
+def test_nonfinite_input_is_reported():
+    """A NaN in the initial fields propagates; the step's non-finite check
+    sets the error word and the next sync point returns LBM_ENONFINITE."""
+    from paper_1608_06345_gb300 import lbm
+    rho, u, T = li.uniform_fields(64 * 4, 2)
+    rho[70] = np.nan
+    s = lbm.Solver(0, 1.4, 0.6, 0.6, (64, 4), prec=F32)
+    s.init(rho, u, T)
+    s.step(2)
+    with pytest.raises(lbm.LbmError) as ei:
+        s.moments()
+    assert ei.value.code == lbm.LBM_ENONFINITE
+
+
+def test_checkpoint_roundtrip():
+    from paper_1608_06345_gb300 import lbm
+    shape = (40, 6)
+    fields = fields_for(shape, seed=5)
+    a = lbm.Solver(0, 1.4, 0.6, 0.7, shape, prec=F64)
+    a.init(*fields)
+    a.step(7)
+    raw = np.zeros(lbm.lbm_raw_state_bytes(a.h), dtype=np.uint8)
+    lbm.lbm_get_state(a.h, raw)
+    a.step(5)
+    ra = a.moments()
+    b = lbm.Solver(0, 1.4, 0.6, 0.7, shape, prec=F64)
+    lbm.lbm_set_state(b.h, raw)
+    b.step(5)
+    rb = b.moments()
+    for qa, qb in zip(ra, rb):
+        assert np.array_equal(qa, qb)

@@ -92,3 +92,15 @@ def test_classic_sod_tube_close_to_exact():
     assert riemann.l1_error(R, er) < 0.005
     assert riemann.l1_error(U[0], eu) < 0.005
     assert riemann.l1_error(TT, eT) < 0.008
+
+
+def test_classic_sod_amplifies_roundoff():
+    """Why the classic Sod tube cannot be held to 1e-12 between independent
+    FP64 implementations: after 500 steps the oracle's own result moves by
+    more than 1e-12 when its initial fields move by 4 ulps."""
+    from tests.parity import parity_errors, perturbed, run_oracle
+    shape, bc = (1000, 4), (ora.ZERO_GRADIENT, ora.PERIODIC)
+    fields = li.sod_fields(1000, 4)
+    ref, _ = run_oracle(ora.D2Q37, 1.4, 0.6, 0.6, shape, bc, fields, 500)
+    pert, _ = run_oracle(ora.D2Q37, 1.4, 0.6, 0.6, shape, bc, perturbed(fields, 2.0 ** -53), 500)
+    assert max(parity_errors(pert, ref, 1.4).values()) > 1e-12
