@@ -351,65 +351,64 @@ __global__ void __launch_bounds__(BX) k_step(const S* __restrict__ src, S* __res
 
 // ---------------------------------------------------------------------------
 // init: g = F(rho, u, T), h = (delta/2) T F from FP64 device fields, stored
-// as deviations from the reference equilibrium (computed in FP64)
+// as deviations from the reference equilibrium.  Arithmetic in the compute
+// type C of the instance (FP64 only for FP64 instances); the differences
+// rho - rho0 and T - T0 are taken in FP64 before rounding to C.
 // ---------------------------------------------------------------------------
-template <int LAT, class S>
+template <int LAT, class S, class C>
 __global__ void k_init(S* __restrict__ dst, const double* __restrict__ rho, const double* __restrict__ u,
-                       const double* __restrict__ T, long long N, const Args<double> a,
-                       const Args<float> af) {
+                       const double* __restrict__ T, long long N, const Args<C> a, double rho0, double T0) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= N) return;
-  const double drho = rho[cell] - a.rho0, dT = T[cell] - a.T0;
-  const double uu[3] = {u[cell], u[N + cell], L::D == 3 ? u[2 * N + cell] : 0.0};
+  const C drho = static_cast<C>(rho[cell] - rho0), dT = static_cast<C>(T[cell] - T0);
+  const C uu[3] = {static_cast<C>(u[cell]), static_cast<C>(u[N + cell]),
+                   L::D == 3 ? static_cast<C>(u[2 * N + cell]) : C(0)};
   const long long ps = a.ps;
-  equilibrium_dev<LAT, double>(drho, uu, dT, a, [&](auto I, double dF, double dFh) {
+  equilibrium_dev<LAT, C>(drho, uu, dT, a, [&](auto I, C dF, C dFh) {
     constexpr int i = decltype(I)::value;
-    if constexpr (IsS16<S>::value) {
-      dst[i * ps + cell] = encode<S, float, false>(static_cast<float>(dF), L::grp(i), af);
-      dst[(Q + i) * ps + cell] = encode<S, float, true>(static_cast<float>(dFh), L::grp(i), af);
-    } else {
-      dst[i * ps + cell] = static_cast<S>(dF);
-      dst[(Q + i) * ps + cell] = static_cast<S>(dFh);
-    }
+    dst[i * ps + cell] = encode<S, C, false>(dF, L::grp(i), a);
+    dst[(Q + i) * ps + cell] = encode<S, C, true>(dFh, L::grp(i), a);
   });
 }
 
-// decode a stored value to double (16-bit codec evaluated in FP32, as the step does)
+// ---------------------------------------------------------------------------
+// moments of the stored state (rho, u, T out in FP64), arithmetic in the
+// compute type C; rho0 + drho and T0 + dT are formed in FP64
+// ---------------------------------------------------------------------------
+template <int LAT, class S, class C>
+__global__ void k_moments(const S* __restrict__ src, double* __restrict__ rho, double* __restrict__ u,
+                          double* __restrict__ T, long long N, const Args<C> a, double rho0, double T0) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+  const long long ps = a.ps;
+  C drho, uu[3], dT;
+  moments_dev<LAT, C>(
+      [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        return decode<S, C, false>(src[i * ps + cell], L::grp(i), a);
+      },
+      [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        return decode<S, C, true>(src[(Q + i) * ps + cell], L::grp(i), a);
+      },
+      a, drho, uu, dT);
+  rho[cell] = rho0 + static_cast<double>(drho);
+  u[cell] = static_cast<double>(uu[0]);
+  u[N + cell] = static_cast<double>(uu[1]);
+  if (L::D == 3) u[2 * N + cell] = static_cast<double>(uu[2]);
+  T[cell] = T0 + static_cast<double>(dT);
+}
+
+// decode a stored value to double for the FP64 reductions (16-bit codec in
+// FP32, as the step evaluates it)
 template <class S, bool IS_H>
 __device__ __forceinline__ double decode_d(S v, int g, const Args<float>& af) {
   if constexpr (IsS16<S>::value) return static_cast<double>(decode<S, float, IS_H>(v, g, af));
   else return static_cast<double>(v);
-}
-
-// ---------------------------------------------------------------------------
-// moments of the stored state, in FP64
-// ---------------------------------------------------------------------------
-template <int LAT, class S>
-__global__ void k_moments(const S* __restrict__ src, double* __restrict__ rho, double* __restrict__ u,
-                          double* __restrict__ T, long long N, const Args<double> a, const Args<float> af) {
-  using L = Lat<LAT>;
-  constexpr int Q = L::Q;
-  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= N) return;
-  const long long ps = a.ps;
-  double drho, uu[3], dT;
-  moments_dev<LAT, double>(
-      [&](auto I) {
-        constexpr int i = decltype(I)::value;
-        return decode_d<S, false>(src[i * ps + cell], L::grp(i), af);
-      },
-      [&](auto I) {
-        constexpr int i = decltype(I)::value;
-        return decode_d<S, true>(src[(Q + i) * ps + cell], L::grp(i), af);
-      },
-      a, drho, uu, dT);
-  rho[cell] = a.rho0 + drho;
-  u[cell] = uu[0];
-  u[N + cell] = uu[1];
-  if (L::D == 3) u[2 * N + cell] = uu[2];
-  T[cell] = a.T0 + dT;
 }
 
 // ---------------------------------------------------------------------------

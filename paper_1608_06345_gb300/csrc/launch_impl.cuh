@@ -6,6 +6,12 @@
 
 namespace lbm {
 
+template <class C>
+const Args<C>& args_of(const Instance* inst) {
+  if constexpr (std::is_same<C, double>::value) return inst->ad;
+  else return inst->af;
+}
+
 template <int LAT, class S, class C, int STAGE, int BX>
 cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, const Args<C>& a) {
   const dim3 grid((unsigned)((inst->n[0] + BX - 1) / BX), (unsigned)inst->n[1], (unsigned)inst->n[2]);
@@ -33,10 +39,7 @@ cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, cons
 template <int LAT, class S, class C>
 cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst) {
   const StepShape& sh = inst->shape;
-  const Args<C>* ap;
-  if constexpr (std::is_same<C, double>::value) ap = &inst->ad;
-  else ap = &inst->af;
-  const Args<C>& a = *ap;
+  const Args<C>& a = args_of<C>(inst);
   if constexpr (LAT == 0) {
     if (sh.bx == 256) return launch_step_t<LAT, S, C, 0, 256>(inst, src, dst, a);
     return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a);
@@ -49,22 +52,23 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst) 
 
 inline unsigned blocks_for(long long N, int t) { return (unsigned)((N + t - 1) / t); }
 
-template <int LAT, class S>
+
+template <int LAT, class S, class C>
 cudaError_t launch_init_t(const Instance* inst, void* dst, const double* rho, const double* u, const double* T) {
   constexpr int kT = 128;
   if (inst->N == 0) return cudaSuccess;
-  k_init<LAT, S><<<blocks_for(inst->N, kT), kT, 0, inst->stream>>>(static_cast<S*>(dst), rho, u, T, inst->N,
-                                                                   inst->ad, inst->af);
+  k_init<LAT, S, C><<<blocks_for(inst->N, kT), kT, 0, inst->stream>>>(static_cast<S*>(dst), rho, u, T, inst->N,
+                                                                      args_of<C>(inst), inst->rho0, inst->T0);
   return cudaGetLastError();
 }
 
 
-template <int LAT, class S>
+template <int LAT, class S, class C>
 cudaError_t launch_moments_t(const Instance* inst, const void* src, double* rho, double* u, double* T) {
   constexpr int kT = 128;
   if (inst->N == 0) return cudaSuccess;
-  k_moments<LAT, S><<<blocks_for(inst->N, kT), kT, 0, inst->stream>>>(static_cast<const S*>(src), rho, u, T,
-                                                                      inst->N, inst->ad, inst->af);
+  k_moments<LAT, S, C><<<blocks_for(inst->N, kT), kT, 0, inst->stream>>>(
+      static_cast<const S*>(src), rho, u, T, inst->N, args_of<C>(inst), inst->rho0, inst->T0);
   return cudaGetLastError();
 }
 

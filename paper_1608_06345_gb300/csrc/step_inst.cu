@@ -32,8 +32,8 @@ using ComputeT = float;
 
 extern const Launchers LBM_CAT(kLaunchers, LBM_LAT, LBM_PREC) = {
     &launch_step_shape<LBM_LAT, StoreT, ComputeT>,
-    &launch_init_t<LBM_LAT, StoreT>,
-    &launch_moments_t<LBM_LAT, StoreT>,
+    &launch_init_t<LBM_LAT, StoreT, ComputeT>,
+    &launch_moments_t<LBM_LAT, StoreT, ComputeT>,
     &launch_conserve_t<LBM_LAT, StoreT>,
 };
 

@@ -82,7 +82,9 @@ def test_sod_tube_1000x4(steps, prec):
     gpu, cgpu = run_gpu(0, 1.4, 0.6, 0.6, shape, bc, fields, steps, prec)
     tol = conditioned_tolerance(prec, kappa, steps)
     assert_parity(gpu, ref, 1.4, tol)
-    rtol = 1e-12 if prec == F64 else 1e-6
+    # totals: FP64 to 1e-12; FP32 rounds each population at every step, so
+    # the totals may drift by a few units of FP32 roundoff per step
+    rtol = 1e-12 if prec == F64 else 4.0 * steps * 2.0 ** -24
     np.testing.assert_allclose(cgpu, cref, rtol=rtol, atol=rtol * abs(cref[0]))
 
 
