@@ -124,10 +124,15 @@ int lbm_sync(lbm_handle h);
 /* Time steps taken since the last init. */
 long lbm_steps_done(lbm_handle h);
 
-/* Copy the raw population planes of the current state (2Q planes of N
- * values in the storage type, velocity order of lbm_lattice_table) to or
- * from host memory of lbm_raw_state_bytes() bytes, for checkpoint/restore.
- * Synchronous. */
+/* Copy the raw population planes of the current state to or from host
+ * memory of lbm_raw_state_bytes() bytes, for checkpoint/restore.
+ * Synchronous.  Layout: 2Q planes of N values in the storage type (g for
+ * velocities 0..Q-1, then h), velocity order of lbm_lattice_table.  Values
+ * are deviations from the instance's reference equilibrium gref_i =
+ * F_i(rho0, u = 0, T0), href_i = (delta/2) T0 gref_i: g_i - gref_i and
+ * h_i - href_i for FP64/FP32 storage; (g_i - gref_i)/gref_i and
+ * (h_i - href_i)/hscale_i (hscale_i = href_i, or gref_i when delta = 0) for
+ * 16-bit storage. */
 size_t lbm_raw_state_bytes(lbm_handle h);
 int lbm_get_state(lbm_handle h, void* host, size_t bytes);
 int lbm_set_state(lbm_handle h, const void* host, size_t bytes);
@@ -137,6 +142,31 @@ int lbm_set_state(lbm_handle h, const void* host, size_t bytes);
  * *q = Q; c[Q*D] integer velocities (row-major), w[Q] weights, *r the
  * scaling factor (xi_i = r c_i).  Any output pointer may be NULL. */
 int lbm_lattice_table(int lattice, int* q, int* c, double* w, double* r);
+
+/* Grid totals (as lbm_conserved: out[0] mass, out[1..D] momentum, out[D+1]
+ * energy) of a raw state held in device memory, computed without allocating
+ * anything.  The paper has no counterpart: this serves callers that cannot
+ * call cudaMalloc when they need the totals -- e.g. a serving pool that has
+ * reserved the whole device budget, or code holding populations in its own
+ * arena without a library instance.
+ *  state         device pointer to 2Q planes in the layout of lbm_get_state
+ *                (deviations from the reference equilibrium of rho0, T0),
+ *                plane p at element offset p * plane_stride
+ *  ncells        cells per plane, 0 <= ncells <= 16777216 (4096^2 or 256^3);
+ *                larger sizes fail with LBM_EINVAL
+ *  lattice, prec, gamma, rho0, T0: as given to lbm_create (rho0, T0 <= 0
+ *                mean 1.0)
+ *  stream        cudaStream_t to run on (NULL = default stream); the call
+ *                synchronises it before returning
+ *  out           host array of D + 2 doubles
+ * The block partials live in one static device array of about 160 KB that
+ * every GPU loading the library keeps until exit.  The first call on a
+ * device looks up that array's device address (make it before any stream
+ * capture).  All calls share the array: calls that overlap on the GPU race
+ * and give wrong totals.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+int lbm_conserved_noalloc(int lattice, int prec, double gamma, double rho0, double T0, const void* state,
+                          long long ncells, long long plane_stride, void* stream, double* out);
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);

@@ -157,6 +157,8 @@ int check_status(Instance* I) {
 
 }  // namespace
 
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 StepShape default_shape(int lattice, int prec) {
   if (lattice == LBM_D2Q37) return StepShape{128, 0};
   if (prec == kF32S16F || prec == kF32S16BF) return StepShape{64, 2};

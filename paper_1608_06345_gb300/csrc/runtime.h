@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "kernels.cuh"
 #include "lattice.h"
 
@@ -62,5 +64,8 @@ extern const Launchers kLaunchers_0_0, kLaunchers_0_1, kLaunchers_0_2, kLauncher
 extern const Launchers kLaunchers_1_0, kLaunchers_1_1, kLaunchers_1_2, kLaunchers_1_3;
 
 StepShape default_shape(int lattice, int prec);
+
+// Records msg as this thread's lbm_last_error() and returns code.
+int set_error(int code, const std::string& msg);
 
 }  // namespace lbm

@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4
 # every entry point of include/lbm.h
 EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init_device", "lbm_step",
            "lbm_moments", "lbm_moments_device", "lbm_conserved", "lbm_sync", "lbm_steps_done",
-           "lbm_raw_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_lattice_table", "lbm_last_error"]
+           "lbm_raw_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_lattice_table", "lbm_last_error",
+           "lbm_conserved_noalloc"]
 
 
 class LbmError(RuntimeError):
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = False):
         "lbm_set_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "lbm_lattice_table": (ctypes.c_int, [ctypes.c_int, ip, ip, dp, dp]),
         "lbm_last_error": (ctypes.c_char_p, []),
+        "lbm_conserved_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, vp, ctypes.c_longlong, ctypes.c_longlong, vp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -200,6 +203,16 @@ def lbm_lattice_table(lattice):
                                     w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(r)))
     Q = q.value
     return c[: Q * D].reshape(Q, D).astype(np.int64), w[:Q].copy(), r.value
+
+
+def lbm_conserved_noalloc(lattice, prec, gamma, state, ncells, plane_stride, stream=None, rho0=0.0, T0=0.0):
+    """Totals of a raw device state without any allocation (see include/lbm.h).
+    `state` is a device pointer (int) or a CUDA tensor; returns out[D + 2]."""
+    ptr = state if isinstance(state, int) else _ptr(state)
+    out = np.zeros(2 + dim(lattice))
+    _check(load().lbm_conserved_noalloc(lattice, prec, gamma, rho0, T0, ptr, int(ncells), int(plane_stride),
+                                        stream, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 def lbm_last_error():
