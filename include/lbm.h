@@ -71,8 +71,10 @@ typedef struct {
   void* device_mem;     /* optional caller-owned device buffer of >= lbm_state_bytes()
                            bytes, 256-byte aligned; NULL = the library allocates */
   size_t device_bytes;  /* size of device_mem */
-  double rho0, T0;      /* reference state of the 16-bit storage (ignored otherwise);
-                           0 means 1.0 */
+  double rho0, T0;      /* reference state (rho0, u = 0, T0) whose equilibrium the
+                           stored populations are deviations from; 0 means 1.0.
+                           Exact for every precision; for 16-bit storage pick it
+                           near the flow's mean state */
 } lbm_grid;
 
 /* Device bytes an instance needs: two copies of the 2Q population planes
