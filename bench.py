@@ -362,10 +362,84 @@ def run_ours(args, wl):
         "clocks": clk,
         "cpu_baseline": cpu,
     }
+    if world == 1 and args.workload == "periodic2d" and not args.no_serving:
+        line["serving"] = serving_eval(args)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def serving_eval(args):
+    """Continuous batching of a Poisson stream of shock-tube solves (D2Q37,
+    FP32, Nx log-uniform in [256, 16384] x 4, gamma, density/pressure ratios,
+    tau and 200-2000 steps drawn per request, seed 6) in a pool with an
+    explicit memory budget, against the plain FP64 method (one instance per
+    request, one launch per step, served in arrival order).  Returns a dict."""
+    from paper_1608_06345_gb300 import lbm, serving
+    lbm.load()
+    params = li.serving_requests(n=args.serving_requests, seed=6)
+    reqs = serving.shock_tube_requests(params)
+    budget = args.serving_budget_mb << 20
+
+    def batched(arrivals):
+        pool = lbm.Pool(0, lbm.LBM_F32, budget_bytes=budget, max_instances=512, bundle_steps=args.bundle_steps)
+        recs = serving.serve(reqs, arrivals, serving.PoolBackend(pool))
+        pool.close()
+        return recs
+
+    # warm-up (graph instantiation, first launches) on a few requests
+    warm = lbm.Pool(0, lbm.LBM_F32, budget_bytes=budget, max_instances=512, bundle_steps=args.bundle_steps)
+    serving.serve(reqs[:8], np.zeros(8), serving.PoolBackend(warm))
+    warm.close()
+
+    cap = serving.summarize(batched(np.zeros(len(reqs))))
+    capacity = cap["solves_per_s"]
+    loads = []
+    for f in (0.5, 0.8, 1.0):
+        arr = li.poisson_arrivals(len(reqs), rate=f * capacity, seed=7)
+        s = serving.summarize(batched(arr))
+        s["offered_load"] = f
+        s["rate_per_s"] = f * capacity
+        loads.append(s)
+
+    def make_solver(req):
+        return lbm.Solver(0, req.gamma, req.tau_f, req.tau_g, req.shape, bc=req.bc, prec=lbm.LBM_F64)
+
+    base = None
+    if not args.no_baseline:
+        arr = li.poisson_arrivals(len(reqs), rate=0.8 * capacity, seed=7)
+        base = serving.summarize(serving.serve_baseline(reqs, arr, make_solver))
+        base["offered_load_of_batched_capacity"] = 0.8
+    cells_steps = sum(r.cells * r.steps for r in reqs)
+    return {
+        "workload": f"{len(reqs)} shock-tube solves, D2Q37 FP32, Nx log-uniform [256, 16384] x 4, gamma "
+                    f"U[1.1, 1.67], ratios logU[1, 10], tau U[0.52, 1], steps U[200, 2000], seed 6; pool budget "
+                    f"{args.serving_budget_mb} MB, bundle {args.bundle_steps} steps",
+        "batched_solves_per_s": capacity, "capacity": cap, "poisson": loads,
+        "baseline_fp64_one_per_launch": base,
+        "p99_ms_at_0.8": loads[1]["p99_ms"],
+        "baseline_p99_ms_at_0.8": base["p99_ms"] if base else None,
+        "throughput_vs_baseline": capacity / base["solves_per_s"] if base else None,
+        "cell_updates_requested": cells_steps,
+    }
+
+
+def run_serving(args):
+    import torch
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local if world > 1 else 0)
+    sv = serving_eval(args)
+    cap = sv["capacity"]
+    line = {
+        "metric": "batched solves/s", "value": sv["batched_solves_per_s"], "unit": "solves/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": cap["makespan_s"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": sv["workload"]}, "serving": sv,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -374,10 +448,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="periodic2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="periodic2d", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serving-requests", type=int, default=512)
+    ap.add_argument("--serving-budget-mb", type=int, default=256)
+    ap.add_argument("--bundle-steps", type=int, default=50)
+    ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving summary of the default line")
     args = ap.parse_args()
+    if args.workload == "serving":
+        run_serving(args)
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

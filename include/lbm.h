@@ -170,6 +170,76 @@ int lbm_lattice_table(int lattice, int* q, int* c, double* w, double* r);
 int lbm_conserved_noalloc(int lattice, int prec, double gamma, double rho0, double T0, const void* state,
                           long long ncells, long long plane_stride, void* stream, double* out);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching pool: many independent instances of one lattice and
+ * precision (shock tubes and periodic boxes of different sizes, gamma, tau,
+ * step counts) resident in one device arena and advanced together by one
+ * batched launch per time step.  Instances are admitted against the memory
+ * budget as they arrive and retired when their results are read, between
+ * step bundles; each instance computes exactly what it would alone.
+ * Typical loop: submit arrivals (LBM_EBUSY = wait) -> lbm_pool_run(1) ->
+ * lbm_pool_poll each ticket -> lbm_pool_result for finished ones.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_pool* lbm_pool_handle;
+
+typedef struct {
+  int lattice;          /* lbm_lattice of every instance */
+  int prec;             /* lbm_prec of every instance */
+  size_t budget_bytes;  /* device bytes for instance states (the admission budget) */
+  int max_instances;    /* resident instances at most */
+  int max_tiles;        /* work-list entries at most (0 = sized from the budget) */
+  int bundle_steps;     /* time steps per lbm_pool_run bundle (one CUDA graph) */
+  void* stream;         /* cudaStream_t; NULL = the pool creates its own stream */
+  void* device_mem;     /* optional caller-owned device buffer of >= lbm_pool_bytes(),
+                           256-byte aligned; NULL = the library allocates */
+  size_t device_bytes;
+} lbm_pool_config;
+
+/* Device bytes a pool needs (arena + slot table + work list); 0 if invalid. */
+size_t lbm_pool_bytes(const lbm_pool_config* cfg);
+
+/* Create a pool.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_pool_create(lbm_pool_handle* out, const lbm_pool_config* cfg);
+
+/* Destroy a pool (synchronises; NULL-safe). */
+int lbm_pool_destroy(lbm_pool_handle p);
+
+/* Arena bytes an instance of this grid takes (two population buffers). */
+size_t lbm_pool_instance_bytes(lbm_pool_handle p, const lbm_grid* grid);
+
+/* Admit an instance: validate as lbm_create (grid->prec must equal the
+ * pool's; grid->stream and grid->device_mem are ignored), set it to the
+ * equilibrium of the host fields rho, u, T (as lbm_init) and give it `steps`
+ * time steps to take.  Synchronises the pool stream (the host arrays are
+ * copied when it returns).  LBM_EBUSY if no slot, budget or work-list room
+ * is free now (nothing changes; retry after results are read). */
+int lbm_pool_submit(lbm_pool_handle p, double gamma, double tau_f, double tau_g, const lbm_grid* grid,
+                    const double* rho, const double* u, const double* T, long steps, long long* ticket);
+
+/* Enqueue `bundles` step bundles: each advances every resident instance
+ * that has steps left by up to bundle_steps steps.  Asynchronous. */
+int lbm_pool_run(lbm_pool_handle p, int bundles);
+
+/* Synchronise the pool's stream and read the instances' error words: an
+ * instance that met a non-finite state stops stepping on the device and is
+ * reported finished (its lbm_pool_result returns LBM_ENONFINITE). */
+int lbm_pool_sync(lbm_pool_handle p);
+
+/* *done = 1 once all the instance's steps are enqueued (its result can be
+ * read), else 0; *steps_done gets the steps enqueued so far.  Either pointer
+ * may be NULL.  LBM_EINVAL for an unknown ticket. */
+int lbm_pool_poll(lbm_pool_handle p, long long ticket, int* done, long* steps_done);
+
+/* rho, u, T of a finished instance into host arrays (as lbm_moments), then
+ * retire it and free its memory.  Synchronises.  LBM_EBUSY if it still has
+ * steps left; LBM_ENONFINITE if it met a non-finite state (the arrays are
+ * filled with NaN and the instance is retired all the same). */
+int lbm_pool_result(lbm_pool_handle p, long long ticket, double* rho, double* u, double* T);
+
+/* out[6]: resident instances, finished-but-unread instances, arena bytes in
+ * use, arena bytes, work-list entries, persistent grid blocks. */
+int lbm_pool_stats(lbm_pool_handle p, long long* out);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);
 

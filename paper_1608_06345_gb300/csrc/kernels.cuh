@@ -264,11 +264,10 @@ __device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args
 // Grid: x = blocks of BX cells along a row, y = row, z = plane.
 // ---------------------------------------------------------------------------
 template <int LAT, class S, class C, int STAGE, int BX>
-__global__ void __launch_bounds__(BX) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
+__device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restrict__ dst, const Args<C>& a, int x,
+                                          int y, int z) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
-  const int x = blockIdx.x * BX + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
   const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
   if (x >= nx) return;
   // source offsets for lattice components c = -3..3 (index c + 3)
@@ -346,6 +345,59 @@ __global__ void __launch_bounds__(BX) k_step(const S* __restrict__ src, S* __res
       dst[i * ps + cell] = encode<S, C, false>(gn, L::grp(i), a);
       dst[(Q + i) * ps + cell] = encode<S, C, true>(hn, L::grp(i), a);
     });
+  }
+}
+
+template <int LAT, class S, class C, int STAGE, int BX>
+__global__ void __launch_bounds__(BX) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
+  step_cell<LAT, S, C, STAGE, BX>(src, dst, a, blockIdx.x * BX + threadIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// batched step of a pool of independent instances (continuous batching)
+//
+// Every resident instance has a slot descriptor in device memory (its
+// constants, its two buffers, which buffer is current and how many steps it
+// still has to take) and contributes tiles of BX cells along a row to one
+// flat tile list.  A persistent grid walks the list; tiles of instances with
+// no steps left are skipped.  Each cell runs exactly the arithmetic of the
+// single-instance kernel, so an instance's result does not depend on what
+// else is resident.  k_pool_advance then decrements the step counters and
+// flips the buffers (and stops an instance whose error word is set); a
+// bundle of steps is a CUDA graph of these two kernels.
+// ---------------------------------------------------------------------------
+template <class C>
+struct PoolSlot {
+  Args<C> a;
+  void* buf[2];
+  int cur;         // buffer holding the current state
+  int steps_left;  // steps still to take
+};
+
+template <int LAT, class S, class C, int STAGE, int BX>
+__global__ void __launch_bounds__(BX) k_pool_step(const PoolSlot<C>* __restrict__ slots,
+                                                  const int4* __restrict__ tiles, const int* __restrict__ n_tiles) {
+  const int nt = *n_tiles;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int4 tl = tiles[t];  // slot, x0, y, z
+    const PoolSlot<C>& sl = slots[tl.x];
+    if (sl.steps_left <= 0) continue;
+    const int c = sl.cur;
+    step_cell<LAT, S, C, STAGE, BX>(static_cast<const S*>(sl.buf[c]), static_cast<S*>(sl.buf[c ^ 1]), sl.a,
+                                    tl.y + (int)threadIdx.x, tl.z, tl.w);
+  }
+}
+
+template <class C>
+__global__ void k_pool_advance(PoolSlot<C>* __restrict__ slots, int nslots) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nslots && slots[i].steps_left > 0) {
+    if (*slots[i].a.flag) {
+      slots[i].steps_left = 0;  // a non-finite instance takes no further steps
+    } else {
+      slots[i].steps_left -= 1;
+      slots[i].cur ^= 1;
+    }
   }
 }
 

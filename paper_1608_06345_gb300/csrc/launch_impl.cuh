@@ -50,6 +50,49 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst) 
   }
 }
 
+// pool: the shape of the batched step per (lattice, storage)
+template <int LAT, class S>
+struct PoolShape {
+  static constexpr int kStage = (LAT == 0) ? 0 : (sizeof(S) >= 4 ? 1 : 2);
+  static constexpr int kBX = (LAT == 0) ? 128 : 64;
+};
+
+template <int LAT, class S, class C>
+cudaError_t launch_pool_step_t(const PoolLaunch& pl) {
+  using PS = PoolShape<LAT, S>;
+  auto kern = k_pool_step<LAT, S, C, PS::kStage, PS::kBX>;
+  // the shared-memory opt-in was set by pool_grid_t at pool creation (outside
+  // any stream capture)
+  const size_t smem = (PS::kStage != 0) ? sizeof(S) * 2 * Lat<LAT>::Q * PS::kBX : 0;
+  kern<<<pl.grid, PS::kBX, smem, pl.stream>>>(static_cast<const PoolSlot<C>*>(pl.slots), pl.tiles, pl.ntiles);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_pool_advance_t(const PoolLaunch& pl) {
+  const int t = 128;
+  k_pool_advance<C><<<(pl.nslots + t - 1) / t, t, 0, pl.stream>>>(static_cast<PoolSlot<C>*>(pl.slots), pl.nslots);
+  return cudaGetLastError();
+}
+
+// persistent grid of the batched step: resident blocks per SM x SMs
+template <int LAT, class S, class C>
+int pool_grid_t() {
+  using PS = PoolShape<LAT, S>;
+  const size_t smem = (PS::kStage != 0) ? sizeof(S) * 2 * Lat<LAT>::Q * PS::kBX : 0;
+  auto kern = k_pool_step<LAT, S, C, PS::kStage, PS::kBX>;
+  if (smem && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PS::kBX, smem) != cudaSuccess) return 0;
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+template <int LAT, class S>
+constexpr int pool_tile_cells() { return PoolShape<LAT, S>::kBX; }
+
 inline unsigned blocks_for(long long N, int t) { return (unsigned)((N + t - 1) / t); }
 
 

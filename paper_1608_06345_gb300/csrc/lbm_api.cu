@@ -122,11 +122,7 @@ void fill_args(const Instance& I, Args<C>* a) {
   a->flag = I.flag;
 }
 
-const Launchers& launchers_of(const Instance* I) {
-  static const Launchers* table[2][4] = {{&kLaunchers_0_0, &kLaunchers_0_1, &kLaunchers_0_2, &kLaunchers_0_3},
-                                         {&kLaunchers_1_0, &kLaunchers_1_1, &kLaunchers_1_2, &kLaunchers_1_3}};
-  return *table[I->lattice][I->prec];
-}
+const Launchers& launchers_of(const Instance* I) { return launchers_for(I->lattice, I->prec); }
 cudaError_t launch_step(const Instance* I, const void* src, void* dst) { return launchers_of(I).step(I, src, dst); }
 cudaError_t launch_init(const Instance* I, void* dst, const double* rho, const double* u, const double* T) {
   return launchers_of(I).init(I, dst, rho, u, T);
@@ -165,6 +161,55 @@ StepShape default_shape(int lattice, int prec) {
   return StepShape{64, 1};
 }
 
+
+int prepare_instance(Instance* I, int lattice, double gamma, double tau_f, double tau_g, const lbm_grid* grid) {
+  int D, Q;
+  std::string msg = check_grid(lattice, grid, &D, &Q);
+  if (!msg.empty()) return fail(LBM_EINVAL, msg);
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(LBM_EINVAL, "gamma must be > 1");
+  double delta = 2.0 / (gamma - 1.0) - D;
+  if (delta < -1e-12) return fail(LBM_EINVAL, "gamma gives delta < 0 (gamma must be <= (D+2)/D)");
+  if (delta < 0.0) delta = 0.0;
+  if (!(tau_f > 0.5) || !(tau_g > 0.5) || !std::isfinite(tau_f) || !std::isfinite(tau_g))
+    return fail(LBM_EINVAL, "tau_f and tau_g must be > 0.5");
+  I->lattice = lattice;
+  I->prec = grid->prec;
+  I->D = D;
+  I->Q = Q;
+  I->n[0] = grid->nx;
+  I->n[1] = grid->ny;
+  I->n[2] = grid->nz;
+  for (int a = 0; a < 3; ++a) I->bc[a] = grid->bc[a];
+  I->N = (long long)grid->nx * grid->ny * grid->nz;
+  I->ps = (long long)round_up((size_t)I->N, 64);
+  I->word = word_of(grid->prec);
+  I->buf_bytes = buffer_bytes(Q, I->N, grid->prec);
+  I->stream = static_cast<cudaStream_t>(grid->stream);
+  I->gamma = gamma;
+  I->delta = delta;
+  I->tau_f = tau_f;
+  I->tau_g = tau_g;
+  I->rho0 = grid->rho0 > 0.0 ? grid->rho0 : 1.0;
+  I->T0 = grid->T0 > 0.0 ? grid->T0 : 1.0;
+  I->shape = default_shape(lattice, grid->prec);
+  if (build_lattice_table(lattice, &I->table) != 0) return fail(LBM_EINVAL, "lattice table refinement failed");
+  I->G = I->table.G;
+  return LBM_OK;
+}
+
+void fill_instance_args(Instance* I) {
+  fill_args(*I, &I->ad);
+  fill_args(*I, &I->af);
+}
+
+size_t instance_buffer_bytes(int Q, long long N, int prec) { return buffer_bytes(Q, N, prec); }
+
+const Launchers& launchers_for(int lattice, int prec) {
+  static const Launchers* table[2][4] = {{&kLaunchers_0_0, &kLaunchers_0_1, &kLaunchers_0_2, &kLaunchers_0_3},
+                                         {&kLaunchers_1_0, &kLaunchers_1_1, &kLaunchers_1_2, &kLaunchers_1_3}};
+  return *table[lattice][prec];
+}
+
 }  // namespace lbm
 
 // The opaque handle type of the C ABI is the runtime's instance record.
@@ -184,45 +229,13 @@ size_t lbm_state_bytes(int lattice, const lbm_grid* grid) {
 int lbm_create(lbm_handle* out, int lattice, double gamma, double tau_f, double tau_g, const lbm_grid* grid) {
   if (!out) return fail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
-  int D, Q;
-  std::string msg = check_grid(lattice, grid, &D, &Q);
-  if (!msg.empty()) return fail(LBM_EINVAL, msg);
-  if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(LBM_EINVAL, "gamma must be > 1");
-  double delta = 2.0 / (gamma - 1.0) - D;
-  if (delta < -1e-12) return fail(LBM_EINVAL, "gamma gives delta < 0 (gamma must be <= (D+2)/D)");
-  if (delta < 0.0) delta = 0.0;
-  if (!(tau_f > 0.5) || !(tau_g > 0.5) || !std::isfinite(tau_f) || !std::isfinite(tau_g))
-    return fail(LBM_EINVAL, "tau_f and tau_g must be > 0.5");
-  const double rho0 = grid->rho0 > 0.0 ? grid->rho0 : 1.0;
-  const double T0 = grid->T0 > 0.0 ? grid->T0 : 1.0;
-
   lbm_instance* I = new (std::nothrow) lbm_instance();
   if (!I) return fail(LBM_ENOMEM, "host allocation failed");
-  I->lattice = lattice;
-  I->prec = grid->prec;
-  I->D = D;
-  I->Q = Q;
-  I->n[0] = grid->nx;
-  I->n[1] = grid->ny;
-  I->n[2] = grid->nz;
-  for (int a = 0; a < 3; ++a) I->bc[a] = grid->bc[a];
-  I->N = (long long)grid->nx * grid->ny * grid->nz;
-  I->ps = (long long)round_up((size_t)I->N, 64);
-  I->word = word_of(grid->prec);
-  I->buf_bytes = buffer_bytes(Q, I->N, grid->prec);
-  I->stream = static_cast<cudaStream_t>(grid->stream);
-  I->gamma = gamma;
-  I->delta = delta;
-  I->tau_f = tau_f;
-  I->tau_g = tau_g;
-  I->rho0 = rho0;
-  I->T0 = T0;
-  I->shape = default_shape(lattice, grid->prec);
-  if (build_lattice_table(lattice, &I->table) != 0) {
+  int rc = prepare_instance(I, lattice, gamma, tau_f, tau_g, grid);
+  if (rc != LBM_OK) {
     delete I;
-    return fail(LBM_EINVAL, "lattice table refinement failed");
+    return rc;
   }
-  I->G = I->table.G;
 
   const size_t need = 2 * I->buf_bytes + kTailBytes;
   if (grid->device_mem) {
@@ -252,8 +265,7 @@ int lbm_create(lbm_handle* out, int lattice, double gamma, double tau_f, double 
   I->red_out = reinterpret_cast<double*>(tail + 256);
   I->red_partial = reinterpret_cast<double*>(tail + 512);
   I->cur = 0;
-  fill_args(*I, &I->ad);
-  fill_args(*I, &I->af);
+  fill_instance_args(I);
   cudaError_t e = cudaMemsetAsync(tail, 0, kTailBytes, I->stream);
   if (e != cudaSuccess) {
     if (I->own_mem) cudaFree(I->mem);

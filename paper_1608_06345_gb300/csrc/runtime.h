@@ -8,6 +8,7 @@
 
 #include <string>
 
+#include "../../include/lbm.h"
 #include "kernels.cuh"
 #include "lattice.h"
 
@@ -50,6 +51,16 @@ constexpr size_t kTailBytes = 256 /*flag*/ + 256 /*red_out*/ + sizeof(double) * 
 
 inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Arguments of the pool launchers (device pointers of the pool tables).
+struct PoolLaunch {
+  void* slots;          // PoolSlot<C>[nslots]
+  const int4* tiles;    // tile list: slot, x0, y, z
+  const int* ntiles;    // device: tiles in the list
+  int nslots;
+  int grid;             // persistent grid of the batched step
+  cudaStream_t stream;
+};
+
 // Launchers of one (lattice, precision) pair; each pair is compiled as its
 // own object from step_inst.cu.  All launch on inst->stream and return the
 // CUDA error of the launch.
@@ -58,6 +69,10 @@ struct Launchers {
   cudaError_t (*init)(const Instance* inst, void* dst, const double* rho, const double* u, const double* T);
   cudaError_t (*moments)(const Instance* inst, const void* src, double* rho, double* u, double* T);
   cudaError_t (*conserve)(const Instance* inst, const void* src, double* partial, int nblocks);
+  cudaError_t (*pool_step)(const PoolLaunch& pl);
+  cudaError_t (*pool_advance)(const PoolLaunch& pl);
+  int (*pool_grid)();
+  int pool_tile_cells;  // cells per tile along x
 };
 
 extern const Launchers kLaunchers_0_0, kLaunchers_0_1, kLaunchers_0_2, kLaunchers_0_3;
@@ -67,5 +82,15 @@ StepShape default_shape(int lattice, int prec);
 
 // Records msg as this thread's lbm_last_error() and returns code.
 int set_error(int code, const std::string& msg);
+
+
+// Validates the parameters of an instance and fills everything but its
+// memory (buffers, flag, reduction scratch) and its Args; returns a status.
+int prepare_instance(Instance* I, int lattice, double gamma, double tau_f, double tau_g, const lbm_grid* grid);
+// Fills I->ad and I->af from the instance (after its flag pointer is set).
+void fill_instance_args(Instance* I);
+// Bytes of one population buffer (2Q planes, 256-byte rounded).
+size_t instance_buffer_bytes(int Q, long long N, int prec);
+const Launchers& launchers_for(int lattice, int prec);
 
 }  // namespace lbm

@@ -35,6 +35,10 @@ extern const Launchers LBM_CAT(kLaunchers, LBM_LAT, LBM_PREC) = {
     &launch_init_t<LBM_LAT, StoreT, ComputeT>,
     &launch_moments_t<LBM_LAT, StoreT, ComputeT>,
     &launch_conserve_t<LBM_LAT, StoreT>,
+    &launch_pool_step_t<LBM_LAT, StoreT, ComputeT>,
+    &launch_pool_advance_t<ComputeT>,
+    &pool_grid_t<LBM_LAT, StoreT, ComputeT>,
+    pool_tile_cells<LBM_LAT, StoreT>(),
 };
 
 }  // namespace lbm

@@ -31,7 +31,9 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4
 EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init_device", "lbm_step",
            "lbm_moments", "lbm_moments_device", "lbm_conserved", "lbm_sync", "lbm_steps_done",
            "lbm_raw_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_lattice_table", "lbm_last_error",
-           "lbm_conserved_noalloc"]
+           "lbm_conserved_noalloc", "lbm_pool_bytes", "lbm_pool_create", "lbm_pool_destroy",
+           "lbm_pool_instance_bytes", "lbm_pool_submit", "lbm_pool_run", "lbm_pool_sync", "lbm_pool_poll",
+           "lbm_pool_result", "lbm_pool_stats"]
 
 
 class LbmError(RuntimeError):
@@ -45,6 +47,12 @@ class lbm_grid(ctypes.Structure):
                 ("bc", ctypes.c_int * 3), ("prec", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("device_mem", ctypes.c_void_p), ("device_bytes", ctypes.c_size_t),
                 ("rho0", ctypes.c_double), ("T0", ctypes.c_double)]
+
+
+class lbm_pool_config(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("prec", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
+                ("max_instances", ctypes.c_int), ("max_tiles", ctypes.c_int), ("bundle_steps", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("device_mem", ctypes.c_void_p), ("device_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -88,6 +96,18 @@ def load(build_if_missing: bool = False):
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_conserved_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, vp, ctypes.c_longlong, ctypes.c_longlong, vp, dp]),
+        "lbm_pool_bytes": (ctypes.c_size_t, [ctypes.POINTER(lbm_pool_config)]),
+        "lbm_pool_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(lbm_pool_config)]),
+        "lbm_pool_destroy": (ctypes.c_int, [vp]),
+        "lbm_pool_instance_bytes": (ctypes.c_size_t, [vp, gp]),
+        "lbm_pool_submit": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, gp, vp, vp, vp,
+                                           ctypes.c_long, ctypes.POINTER(ctypes.c_longlong)]),
+        "lbm_pool_run": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_pool_sync": (ctypes.c_int, [vp]),
+        "lbm_pool_poll": (ctypes.c_int, [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_long)]),
+        "lbm_pool_result": (ctypes.c_int, [vp, ctypes.c_longlong, vp, vp, vp]),
+        "lbm_pool_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -291,3 +311,132 @@ class Solver:
 
     def sync(self):
         lbm_sync(self.h)
+
+
+# ---------------------------------------------------------------------------
+# continuous-batching pool
+# ---------------------------------------------------------------------------
+def make_pool_config(lattice, prec, budget_bytes, max_instances, bundle_steps, max_tiles=0, stream=None,
+                     device_mem=None, device_bytes=0):
+    c = lbm_pool_config()
+    c.lattice, c.prec = lattice, prec
+    c.budget_bytes = int(budget_bytes)
+    c.max_instances, c.max_tiles, c.bundle_steps = int(max_instances), int(max_tiles), int(bundle_steps)
+    c.stream, c.device_mem, c.device_bytes = stream, device_mem, device_bytes
+    return c
+
+
+def lbm_pool_bytes(cfg):
+    return load().lbm_pool_bytes(ctypes.byref(cfg))
+
+
+def lbm_pool_create(cfg):
+    h = ctypes.c_void_p()
+    _check(load().lbm_pool_create(ctypes.byref(h), ctypes.byref(cfg)))
+    return h
+
+
+def lbm_pool_destroy(p):
+    return _check(load().lbm_pool_destroy(p))
+
+
+def lbm_pool_instance_bytes(p, grid):
+    return load().lbm_pool_instance_bytes(p, ctypes.byref(grid))
+
+
+def lbm_pool_submit(p, gamma, tau_f, tau_g, grid, rho, u, T, steps):
+    """Ticket of the admitted instance, or None when the pool is busy (LBM_EBUSY)."""
+    t = ctypes.c_longlong()
+    rc = load().lbm_pool_submit(p, gamma, tau_f, tau_g, ctypes.byref(grid), _ptr(rho), _ptr(u), _ptr(T),
+                                int(steps), ctypes.byref(t))
+    if rc == LBM_EBUSY:
+        return None
+    _check(rc)
+    return t.value
+
+
+def lbm_pool_run(p, bundles=1):
+    return _check(load().lbm_pool_run(p, int(bundles)))
+
+
+def lbm_pool_sync(p):
+    return _check(load().lbm_pool_sync(p))
+
+
+def lbm_pool_poll(p, ticket):
+    done = ctypes.c_int()
+    steps = ctypes.c_long()
+    _check(load().lbm_pool_poll(p, ticket, ctypes.byref(done), ctypes.byref(steps)))
+    return bool(done.value), steps.value
+
+
+def lbm_pool_result(p, ticket, rho, u, T):
+    """Returns the status (LBM_OK or LBM_ENONFINITE); other errors raise."""
+    rc = load().lbm_pool_result(p, ticket, _ptr(rho), _ptr(u), _ptr(T))
+    if rc not in (LBM_OK, LBM_ENONFINITE):
+        _check(rc)
+    return rc
+
+
+def lbm_pool_stats(p):
+    out = (ctypes.c_longlong * 6)()
+    _check(load().lbm_pool_stats(p, out))
+    keys = ("resident", "finished", "bytes_used", "bytes_budget", "tiles", "grid")
+    return dict(zip(keys, list(out)))
+
+
+class Pool:
+    """A continuous-batching pool on the current CUDA device; its device
+    memory is a torch tensor of lbm_pool_bytes (torch's allocator)."""
+
+    def __init__(self, lattice, prec, budget_bytes, max_instances=512, bundle_steps=50, stream=None):
+        import torch
+        self.lattice, self.prec, self.D = lattice, prec, dim(lattice)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        cfg = make_pool_config(lattice, prec, budget_bytes, max_instances, bundle_steps,
+                               stream=self.stream.cuda_stream)
+        nbytes = lbm_pool_bytes(cfg)
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "invalid pool configuration")
+        with torch.cuda.stream(self.stream):
+            self.mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        cfg.device_mem, cfg.device_bytes = self.mem.data_ptr(), nbytes
+        torch.cuda.synchronize()
+        self.h = lbm_pool_create(cfg)
+        self.bundle_steps = bundle_steps
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lbm_pool_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, gamma, tau_f, tau_g, shape, bc, fields, steps, rho0=0.0, T0=0.0):
+        grid = make_grid(shape, bc=bc, prec=self.prec, rho0=rho0, T0=T0)
+        rho, u, T = (np.ascontiguousarray(a, dtype=np.float64) for a in fields)
+        return lbm_pool_submit(self.h, gamma, tau_f, tau_g, grid, rho, u, T, steps)
+
+    def instance_bytes(self, shape):
+        return lbm_pool_instance_bytes(self.h, make_grid(shape, prec=self.prec))
+
+    def run(self, bundles=1):
+        lbm_pool_run(self.h, bundles)
+
+    def sync(self):
+        lbm_pool_sync(self.h)
+
+    def poll(self, ticket):
+        return lbm_pool_poll(self.h, ticket)
+
+    def result(self, ticket, N):
+        rho, u, T = np.zeros(N), np.zeros(self.D * N), np.zeros(N)
+        rc = lbm_pool_result(self.h, ticket, rho, u, T)
+        return rc, (rho, u.reshape(self.D, N), T)
+
+    def stats(self):
+        return lbm_pool_stats(self.h)
