@@ -270,6 +270,12 @@ def run_ours(args, wl):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # pick the fastest compiled launch shape on this instance (trials write
+    # only the idle buffer; the state is untouched)
+    from paper_1608_06345_gb300 import autotune
+    solver.init(d_rho, d_u, d_T)
+    tuned = autotune.tune(solver, reps=5, cache_path=None)
+
     for _ in range(max(args.warmup, 0)):
         bench_step()
     solver.sync()
@@ -353,7 +359,8 @@ def run_ours(args, wl):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": key, "bytes_per_cell_update": bytes_per_cell,
-                     "step_kernel_us": step_kernel_s * 1e6, "peak_kind": peak_kind},
+                     "step_kernel_us": step_kernel_s * 1e6, "peak_kind": peak_kind,
+                     "shape": {"stage": tuned["stage"], "block": tuned["block"], "index": tuned["index"]}},
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": (2 + D) * N * 8,
                 "d2h_bytes_per_step": (2 + D) * N * 8,
                 "note": "per bench step = one solve through lbm_init (pinned host fields) + lbm_step + "

@@ -170,6 +170,25 @@ int lbm_lattice_table(int lattice, int* q, int* c, double* w, double* r);
 int lbm_conserved_noalloc(int lattice, int prec, double gamma, double rho0, double T0, const void* state,
                           long long ncells, long long plane_stride, void* stream, double* out);
 
+/* Launch shapes of the step kernel.  Each (lattice, precision) has a small
+ * table of compiled candidates (how the pulled values are staged --
+ * registers, shared memory by cp.async, or g in registers and h in shared
+ * memory -- and the cells per thread block); index 0 is the default.
+ * lbm_shape_info describes candidate `index` (LBM_EINVAL past the end). */
+int lbm_shape_info(int lattice, int prec, int index, int* stage, int* block);
+
+/* Select a candidate shape for this instance's steps. */
+int lbm_set_shape(lbm_handle h, int index);
+
+/* Current shape index of the instance (-1 for NULL). */
+int lbm_get_shape(lbm_handle h);
+
+/* Time every candidate shape on this instance's own buffers (reps launches
+ * each, CUDA events on its stream; the trials write only the idle buffer,
+ * so the state does not change), select the fastest and return its index
+ * and mean time per step in microseconds.  Synchronises. */
+int lbm_autotune(lbm_handle h, int reps, int* best_index, double* best_us);
+
 /* ------------------------------------------------------------------------
  * Continuous-batching pool: many independent instances of one lattice and
  * precision (shock tubes and periodic boxes of different sizes, gamma, tau,

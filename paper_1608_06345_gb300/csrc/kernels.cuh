@@ -153,57 +153,90 @@ __device__ __forceinline__ S encode(C v, int g, const Args<C>& a) {
 // and the deviation from gref = w rho0 (1 + pref):
 //   dF_i = w [drho (1 + P) + rho0 (P - pref)] + w rho [A1 s + A2 s^2 + ...]
 //   dFh_i = (delta/2) (T dF_i + dT gref_i)
-// emit(i, dF_i, dFh_i) is called for every velocity.
 // ---------------------------------------------------------------------------
-template <int LAT, class C, class Emit>
-__device__ __forceinline__ void equilibrium_dev(C drho, const C (&u)[3], C dT, const Args<C>& a, Emit&& emit) {
+template <int LAT, class C>
+struct EqCoef {
+  // per-cell polynomials in the group's x2 (see above); the per-group
+  // coefficients are formed just before that group's velocities are emitted
+  C pa, pb, pc, be0, be1, ga0, ga1;
+  C rho, drho;
+  C ur[3];  // r u
+  C T, dT;
+};
+
+template <int LAT, class C>
+__device__ __forceinline__ void eq_coeffs(C drho, const C (&u)[3], C dT, const Args<C>& a, EqCoef<LAT, C>& k) {
   using L = Lat<LAT>;
   constexpr C D = C(L::D);
-  const C rho = a.rho0 + drho;
-  const C T = a.T0 + dT;
+  k.rho = a.rho0 + drho;
+  k.drho = drho;
+  k.T = a.T0 + dT;
+  k.dT = dT;
   const C t = a.t0 + dT;
   const C u2 = u[0] * u[0] + u[1] * u[1] + (L::D == 3 ? u[2] * u[2] : C(0));
   // P = pa + pb x2 + pc x2^2;  A1 = be0 + be1 x2;  A2 = ga0 + ga1 x2
-  const C pa = -C(0.5) * u2 - C(0.5) * D * t + C(0.125) * u2 * u2 + C(0.25) * (D + C(2)) * t * u2 +
-               C(0.125) * D * (D + C(2)) * t * t;
-  const C pb = C(0.5) * t - C(0.25) * t * u2 - C(0.25) * (D + C(2)) * t * t;
-  const C pc = C(0.125) * t * t;
-  const C be0 = C(1) - C(0.5) * u2 - C(0.5) * (D + C(2)) * t;
-  const C be1 = C(0.5) * t;
-  const C ga0 = C(0.5) - C(0.25) * u2 - C(0.25) * (D + C(4)) * t;
-  const C ga1 = C(0.25) * t;
-  C c0[L::G], c1[L::G], c2[L::G], c3[L::G], c4[L::G], hr[L::G];
-#pragma unroll
-  for (int g = 0; g < L::G; ++g) {
+  k.pa = -C(0.5) * u2 - C(0.5) * D * t + C(0.125) * u2 * u2 + C(0.25) * (D + C(2)) * t * u2 +
+         C(0.125) * D * (D + C(2)) * t * t;
+  k.pb = C(0.5) * t - C(0.25) * t * u2 - C(0.25) * (D + C(2)) * t * t;
+  k.pc = C(0.125) * t * t;
+  k.be0 = C(1) - C(0.5) * u2 - C(0.5) * (D + C(2)) * t;
+  k.be1 = C(0.5) * t;
+  k.ga0 = C(0.5) - C(0.25) * u2 - C(0.25) * (D + C(4)) * t;
+  k.ga1 = C(0.25) * t;
+  k.ur[0] = a.r * u[0];
+  k.ur[1] = a.r * u[1];
+  k.ur[2] = L::D == 3 ? a.r * u[2] : C(0);
+}
+
+// emit(I, dF_i) for every velocity i: the rest velocity, then the (c, -c)
+// pairs sharing the even part of the polynomial in s.  Velocities are
+// ordered by group, so a group's coefficients c0..c4 are formed once, at its
+// first pair, and are dead after its last.
+template <int LAT, class C, class Emit>
+__device__ __forceinline__ void eq_emit(const EqCoef<LAT, C>& k, const Args<C>& a, Emit&& emit) {
+  using L = Lat<LAT>;
+  C c0, c1, c2, c3, c4;
+  auto group = [&](int g) {
     const C x2 = a.x2g[g];
-    const C P = fma(x2, fma(x2, pc, pb), pa);
-    const C W = a.wg[g] * rho;
-    c0[g] = a.wg[g] * fma(drho, C(1) + P, a.rho0 * (P - a.pref[g]));
-    c1[g] = W * fma(be1, x2, be0);
-    c2[g] = W * fma(ga1, x2, ga0);
-    c3[g] = W * C(1.0 / 6.0);
-    c4[g] = W * C(1.0 / 24.0);
-    hr[g] = dT * a.gref[g];
-  }
-  const C ur[3] = {a.r * u[0], a.r * u[1], L::D == 3 ? a.r * u[2] : C(0)};
-  const C hd = a.half_delta;
-  emit(std::integral_constant<int, 0>{}, c0[0], hd * fma(T, c0[0], hr[0]));
+    const C P = fma(x2, fma(x2, k.pc, k.pb), k.pa);
+    const C W = a.wg[g] * k.rho;
+    c0 = a.wg[g] * fma(k.drho, C(1) + P, a.rho0 * (P - a.pref[g]));
+    c1 = W * fma(k.be1, x2, k.be0);
+    c2 = W * fma(k.ga1, x2, k.ga0);
+    c3 = W * C(1.0 / 6.0);
+    c4 = W * C(1.0 / 24.0);
+  };
+  group(0);
+  emit(std::integral_constant<int, 0>{}, c0);
   static_for<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if constexpr (i % 2 == 1) {
       constexpr int g = L::grp(i);
+      if constexpr (L::grp(i - 1) != g) group(g);
       constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
       C s = C(0);
-      if constexpr (cx != 0) s = fma(C(cx), ur[0], s);
-      if constexpr (cy != 0) s = fma(C(cy), ur[1], s);
-      if constexpr (cz != 0) s = fma(C(cz), ur[2], s);
+      if constexpr (cx != 0) s = fma(C(cx), k.ur[0], s);
+      if constexpr (cy != 0) s = fma(C(cy), k.ur[1], s);
+      if constexpr (cz != 0) s = fma(C(cz), k.ur[2], s);
       const C s2 = s * s;
-      const C e = fma(s2, fma(s2, c4[g], c2[g]), c0[g]);
-      const C o = s * fma(s2, c3[g], c1[g]);
-      const C fp = e + o, fm = e - o;
-      emit(std::integral_constant<int, i>{}, fp, hd * fma(T, fp, hr[g]));
-      emit(std::integral_constant<int, i + 1>{}, fm, hd * fma(T, fm, hr[g]));
+      const C e = fma(s2, fma(s2, c4, c2), c0);
+      const C o = s * fma(s2, c3, c1);
+      emit(std::integral_constant<int, i>{}, e + o);
+      emit(std::integral_constant<int, i + 1>{}, e - o);
     }
+  });
+}
+
+// dF and dFh of every velocity (used by the init kernel)
+template <int LAT, class C, class Emit>
+__device__ __forceinline__ void equilibrium_dev(C drho, const C (&u)[3], C dT, const Args<C>& a, Emit&& emit) {
+  using L = Lat<LAT>;
+  EqCoef<LAT, C> k;
+  eq_coeffs<LAT, C>(drho, u, dT, a, k);
+  const C hd = a.half_delta;
+  eq_emit<LAT, C>(k, a, [&](auto I, C dF) {
+    constexpr int g = L::grp(decltype(I)::value);
+    emit(I, dF, hd * fma(k.T, dF, dT * a.gref[g]));
   });
 }
 
@@ -213,9 +246,13 @@ __device__ __forceinline__ void equilibrium_dev(C drho, const C (&u)[3], C dT, c
 __device__ __forceinline__ int pull_coord(int p, int c, int n, int bc) {
   int q = p - c;
   if (bc == kPeriodic) {
-    // n >= 1 and |c| <= 3: at most three corrections
-    while (q < 0) q += n;
-    while (q >= n) q -= n;
+    if (n >= 4) {  // one correction at most
+      q = (q < 0) ? q + n : q;
+      q = (q >= n) ? q - n : q;
+    } else {  // n >= 1 and |c| <= 3: at most three corrections
+      while (q < 0) q += n;
+      while (q >= n) q -= n;
+    }
   } else {
     q = q < 0 ? 0 : (q > n - 1 ? n - 1 : q);
   }
@@ -223,7 +260,8 @@ __device__ __forceinline__ int pull_coord(int p, int c, int n, int bc) {
 }
 
 // ---------------------------------------------------------------------------
-// moments of a cell from the deviations (Eq. (14), (15))
+// moments of a cell from the deviations (Eq. (14), (15)), taken over the
+// (c, -c) pairs: sum and difference of the pair
 //   drho = sum dg, rho = rho0 + drho, rho u = r sum c dg,
 //   rho E = rho0 (D + delta) T0 / 2 + dK + dH with dK = r^2/2 sum c^2 dg, dH = sum dh,
 //   T = (2E - u^2)/(D + delta) = T0 + dT,
@@ -233,16 +271,21 @@ template <int LAT, class C, class GetG, class GetH>
 __device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args<C>& a, C& drho, C (&u)[3],
                                             C& dT) {
   using L = Lat<LAT>;
-  C m = C(0), jx = C(0), jy = C(0), jz = C(0), k2 = C(0), H = C(0);
+  C m = getg(std::integral_constant<int, 0>{});
+  C H = geth(std::integral_constant<int, 0>{});
+  C jx = C(0), jy = C(0), jz = C(0), k2 = C(0);
   static_for<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    const C gi = getg(I);
-    m += gi;
-    if constexpr (L::cx(i) != 0) jx = fma(C(L::cx(i)), gi, jx);
-    if constexpr (L::cy(i) != 0) jy = fma(C(L::cy(i)), gi, jy);
-    if constexpr (L::cz(i) != 0) jz = fma(C(L::cz(i)), gi, jz);
-    if constexpr (L::c2(i) != 0) k2 = fma(C(L::c2(i)), gi, k2);
-    H += geth(I);
+    if constexpr (i % 2 == 1) {
+      const C gp = getg(I), gm = getg(std::integral_constant<int, i + 1>{});
+      const C sp = gp + gm, df = gp - gm;
+      m += sp;
+      if constexpr (L::cx(i) != 0) jx = fma(C(L::cx(i)), df, jx);
+      if constexpr (L::cy(i) != 0) jy = fma(C(L::cy(i)), df, jy);
+      if constexpr (L::cz(i) != 0) jz = fma(C(L::cz(i)), df, jz);
+      k2 = fma(C(L::c2(i)), sp, k2);
+      H += geth(I) + geth(std::integral_constant<int, i + 1>{});
+    }
   });
   const C rho = a.rho0 + m;
   const C inv = C(1) / rho;
@@ -256,12 +299,43 @@ __device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args
 }
 
 // ---------------------------------------------------------------------------
-// the fused step
+// collide one cell given its pulled deviations and store the result:
+//   g* = g~ + omega_f (dF - g~)
+//   h* = h~ + omega_g (dFh - h~) = (omega_g hd T) dF + (1 - omega_g) h~ + omega_g hd dT gref
+// ---------------------------------------------------------------------------
+template <int LAT, class S, class C, class GetG, class GetH>
+__device__ __forceinline__ void collide_store(GetG&& getg, GetH&& geth, const Args<C>& a, S* __restrict__ dst,
+                                              long long ps, unsigned cell) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  C drho, u[3], dT;
+  moments_dev<LAT, C>(getg, geth, a, drho, u, dT);
+  if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+  EqCoef<LAT, C> k;
+  eq_coeffs<LAT, C>(drho, u, dT, a, k);
+  const C hA = a.omega_g * a.half_delta * k.T;
+  const C om1 = C(1) - a.omega_g;
+  const C hbs = a.omega_g * a.half_delta * dT;
+  eq_emit<LAT, C>(k, a, [&](auto I, C dF) {
+    constexpr int i = decltype(I)::value;
+    constexpr int g = L::grp(i);
+    const C gi = getg(I), hi = geth(I);
+    const C gn = fma(a.omega_f, dF - gi, gi);
+    const C hn = fma(hA, dF, fma(om1, hi, hbs * a.gref[g]));
+    dst[i * ps + cell] = encode<S, C, false>(gn, g, a);
+    dst[(Q + i) * ps + cell] = encode<S, C, true>(hn, g, a);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// the fused step of one cell
 //   STAGE 0: the 2Q pulled values live in registers (D2Q37)
 //   STAGE 1: they are staged in shared memory by 4/8-byte cp.async (D3Q107,
 //            FP32/FP64 storage): no registers held while the loads fly
 //   STAGE 2: staged in shared memory by plain loads (D3Q107, 16-bit storage)
-// Grid: x = blocks of BX cells along a row, y = row, z = plane.
+//   STAGE 3: g in registers, h staged in shared memory by cp.async (D3Q107,
+//            FP32/FP64): half the shared memory per cell of STAGE 1
+// A block covers BX consecutive cells of a row (thread = cell).
 // ---------------------------------------------------------------------------
 template <int LAT, class S, class C, int STAGE, int BX>
 __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restrict__ dst, const Args<C>& a, int x,
@@ -293,17 +367,26 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
       g[i] = decode<S, C, false>(ldg_s(src + i * ps + off), L::grp(i), a);
       h[i] = decode<S, C, true>(ldg_s(src + (Q + i) * ps + off), L::grp(i), a);
     });
-    C drho, u[3], dT;
-    moments_dev<LAT, C>([&](auto I) { return g[decltype(I)::value]; },
-                        [&](auto I) { return h[decltype(I)::value]; }, a, drho, u, dT);
-    if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
-    equilibrium_dev<LAT, C>(drho, u, dT, a, [&](auto I, C dF, C dFh) {
+    collide_store<LAT, S, C>([&](auto I) { return g[decltype(I)::value]; },
+                             [&](auto I) { return h[decltype(I)::value]; }, a, dst, ps, cell);
+  } else if constexpr (STAGE == 3) {
+    static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* sh = reinterpret_cast<S*>(smem_raw);  // [Q][BX]: h only
+    const int t = threadIdx.x;
+    C g[Q];
+    static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const C gn = fma(a.omega_f, dF - g[i], g[i]);
-      const C hn = fma(a.omega_g, dFh - h[i], h[i]);
-      dst[i * ps + cell] = encode<S, C, false>(gn, L::grp(i), a);
-      dst[(Q + i) * ps + cell] = encode<S, C, true>(hn, L::grp(i), a);
+      const unsigned off = src_off(I);
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(sh + i * BX + t);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src + (Q + i) * ps + off),
+                   "n"(sizeof(S)));
+      g[i] = static_cast<C>(ldg_s(src + i * ps + off));
     });
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    collide_store<LAT, S, C>([&](auto I) { return g[decltype(I)::value]; },
+                             [&](auto I) { return static_cast<C>(sh[decltype(I)::value * BX + t]); }, a, dst, ps,
+                             cell);
   } else {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* sg = reinterpret_cast<S*>(smem_raw);  // [2Q][BX]
@@ -326,30 +409,21 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     });
     if constexpr (STAGE == 1) asm volatile("cp.async.wait_all;\n" ::: "memory");
     // each thread reads back only the slots it filled itself
-    auto getg = [&](auto I) {
-      constexpr int i = decltype(I)::value;
-      return decode<S, C, false>(sg[i * BX + t], L::grp(i), a);
-    };
-    auto geth = [&](auto I) {
-      constexpr int i = decltype(I)::value;
-      return decode<S, C, true>(sg[(Q + i) * BX + t], L::grp(i), a);
-    };
-    C drho, u[3], dT;
-    moments_dev<LAT, C>(getg, geth, a, drho, u, dT);
-    if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
-    equilibrium_dev<LAT, C>(drho, u, dT, a, [&](auto I, C dF, C dFh) {
-      constexpr int i = decltype(I)::value;
-      const C gi = getg(I), hi = geth(I);
-      const C gn = fma(a.omega_f, dF - gi, gi);
-      const C hn = fma(a.omega_g, dFh - hi, hi);
-      dst[i * ps + cell] = encode<S, C, false>(gn, L::grp(i), a);
-      dst[(Q + i) * ps + cell] = encode<S, C, true>(hn, L::grp(i), a);
-    });
+    collide_store<LAT, S, C>(
+        [&](auto I) {
+          constexpr int i = decltype(I)::value;
+          return decode<S, C, false>(sg[i * BX + t], L::grp(i), a);
+        },
+        [&](auto I) {
+          constexpr int i = decltype(I)::value;
+          return decode<S, C, true>(sg[(Q + i) * BX + t], L::grp(i), a);
+        },
+        a, dst, ps, cell);
   }
 }
 
-template <int LAT, class S, class C, int STAGE, int BX>
-__global__ void __launch_bounds__(BX) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
+template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1>
+__global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
   step_cell<LAT, S, C, STAGE, BX>(src, dst, a, blockIdx.x * BX + threadIdx.x, blockIdx.y, blockIdx.z);
 }
 

@@ -12,12 +12,19 @@ const Args<C>& args_of(const Instance* inst) {
   else return inst->af;
 }
 
-template <int LAT, class S, class C, int STAGE, int BX>
+// dynamic shared memory of a step shape: none (STAGE 0), h only (STAGE 3),
+// g and h (STAGE 1, 2)
+template <int LAT, class S, int STAGE, int BX>
+constexpr size_t step_smem() {
+  return STAGE == 0 ? 0 : (STAGE == 3 ? 1 : 2) * sizeof(S) * Lat<LAT>::Q * BX;
+}
+
+template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1>
 cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, const Args<C>& a) {
   const dim3 grid((unsigned)((inst->n[0] + BX - 1) / BX), (unsigned)inst->n[1], (unsigned)inst->n[2]);
   size_t smem = 0;
   if constexpr (STAGE != 0) {
-    smem = sizeof(S) * 2 * Lat<LAT>::Q * BX;
+    smem = step_smem<LAT, S, STAGE, BX>();
     // the shared-memory opt-in is a per-device function attribute: set it
     // once per device (bit d of the mask) for this template instance
     static unsigned long long configured = 0;
@@ -25,28 +32,84 @@ cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, cons
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64 || !(configured & (1ull << dev))) {
-      e = cudaFuncSetAttribute(k_step<LAT, S, C, STAGE, BX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_step<LAT, S, C, STAGE, BX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
       if (e != cudaSuccess) return e;
       if (dev < 64) configured |= (1ull << dev);
     }
   }
-  k_step<LAT, S, C, STAGE, BX><<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst),
+  k_step<LAT, S, C, STAGE, BX, MINB><<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst),
                                                                   a);
   return cudaGetLastError();
 }
 
+// Candidate shapes of the step per (lattice, storage), tried by the
+// autotuner; index 0 is the default.  (stage, cells per block, minimum
+// resident blocks per SM requested from the compiler, which caps registers):
+//   D2Q37 FP32/16-bit: (0,128,4) (0,256,2) (0,64,8) (0,128,1)
+//   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)
+//   D3Q107 FP32:       (1,64,1)  (3,64,1)  (3,64,5)  (3,64,6)  (3,128,3)
+//   D3Q107 FP64:       (1,64,1)
+//   D3Q107 16-bit:     (2,64,1)  (2,32,1)
+template <int LAT, class S>
+struct StepShapes {
+  static constexpr int count =
+      (LAT == 0) ? (sizeof(S) == 8 ? 3 : 4) : (sizeof(S) == 4 ? 5 : (sizeof(S) == 8 ? 1 : 2));
+  static void get(int k, int* stage, int* bx, int* minb) {
+    static const int s2[4][3] = {{0, 128, 4}, {0, 256, 2}, {0, 64, 8}, {0, 128, 1}};
+    static const int s2d[3][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}};
+    static const int s3f[5][3] = {{1, 64, 1}, {3, 64, 1}, {3, 64, 5}, {3, 64, 6}, {3, 128, 3}};
+    static const int s3d[1][3] = {{1, 64, 1}};
+    static const int s3h[2][3] = {{2, 64, 1}, {2, 32, 1}};
+    const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : s2)
+                                  : (sizeof(S) == 4 ? s3f : (sizeof(S) == 8 ? s3d : s3h));
+    *stage = t[k][0];
+    *bx = t[k][1];
+    *minb = t[k][2];
+  }
+};
+
+template <int LAT, class S>
+int shape_count_t() { return StepShapes<LAT, S>::count; }
+
+template <int LAT, class S>
+void shape_get_t(int k, int* stage, int* bx) {
+  int minb = 1;
+  StepShapes<LAT, S>::get(k, stage, bx, &minb);
+}
+
 template <int LAT, class S, class C>
 cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst) {
-  const StepShape& sh = inst->shape;
   const Args<C>& a = args_of<C>(inst);
-  if constexpr (LAT == 0) {
-    if (sh.bx == 256) return launch_step_t<LAT, S, C, 0, 256>(inst, src, dst, a);
-    return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a);
-  } else if constexpr (sizeof(S) >= 4) {
+  const int k = inst->shape.index;
+  if constexpr (LAT == 0 && sizeof(S) == 8) {
+    switch (k) {
+      case 1: return launch_step_t<LAT, S, C, 0, 256>(inst, src, dst, a);
+      case 2: return launch_step_t<LAT, S, C, 0, 64>(inst, src, dst, a);
+      default: return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a);
+    }
+  } else if constexpr (LAT == 0) {
+    switch (k) {
+      case 1: return launch_step_t<LAT, S, C, 0, 256, 2>(inst, src, dst, a);
+      case 2: return launch_step_t<LAT, S, C, 0, 64, 8>(inst, src, dst, a);
+      case 3: return launch_step_t<LAT, S, C, 0, 128, 1>(inst, src, dst, a);
+      default: return launch_step_t<LAT, S, C, 0, 128, 4>(inst, src, dst, a);
+    }
+  } else if constexpr (sizeof(S) == 4) {
+    switch (k) {
+      case 1: return launch_step_t<LAT, S, C, 3, 64>(inst, src, dst, a);
+      case 2: return launch_step_t<LAT, S, C, 3, 64, 5>(inst, src, dst, a);
+      case 3: return launch_step_t<LAT, S, C, 3, 64, 6>(inst, src, dst, a);
+      case 4: return launch_step_t<LAT, S, C, 3, 128, 3>(inst, src, dst, a);
+      default: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a);
+    }
+  } else if constexpr (sizeof(S) == 8) {
     return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a);
   } else {
-    return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a);
+    switch (k) {
+      case 1: return launch_step_t<LAT, S, C, 2, 32>(inst, src, dst, a);
+      default: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a);
+    }
   }
 }
 
@@ -63,7 +126,7 @@ cudaError_t launch_pool_step_t(const PoolLaunch& pl) {
   auto kern = k_pool_step<LAT, S, C, PS::kStage, PS::kBX>;
   // the shared-memory opt-in was set by pool_grid_t at pool creation (outside
   // any stream capture)
-  const size_t smem = (PS::kStage != 0) ? sizeof(S) * 2 * Lat<LAT>::Q * PS::kBX : 0;
+  const size_t smem = step_smem<LAT, S, PS::kStage, PS::kBX>();
   kern<<<pl.grid, PS::kBX, smem, pl.stream>>>(static_cast<const PoolSlot<C>*>(pl.slots), pl.tiles, pl.ntiles);
   return cudaGetLastError();
 }
@@ -79,7 +142,7 @@ cudaError_t launch_pool_advance_t(const PoolLaunch& pl) {
 template <int LAT, class S, class C>
 int pool_grid_t() {
   using PS = PoolShape<LAT, S>;
-  const size_t smem = (PS::kStage != 0) ? sizeof(S) * 2 * Lat<LAT>::Q * PS::kBX : 0;
+  const size_t smem = step_smem<LAT, S, PS::kStage, PS::kBX>();
   auto kern = k_pool_step<LAT, S, C, PS::kStage, PS::kBX>;
   if (smem && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;

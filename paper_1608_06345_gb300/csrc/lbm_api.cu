@@ -156,9 +156,9 @@ int check_status(Instance* I) {
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
 
 StepShape default_shape(int lattice, int prec) {
-  if (lattice == LBM_D2Q37) return StepShape{128, 0};
-  if (prec == kF32S16F || prec == kF32S16BF) return StepShape{64, 2};
-  return StepShape{64, 1};
+  (void)lattice;
+  (void)prec;
+  return StepShape{0};
 }
 
 
@@ -426,6 +426,71 @@ int lbm_lattice_table(int lattice, int* q, int* c, double* w, double* r) {
     if (w) w[i] = t.wg[L.grp[i]];
   }
   if (r) *r = t.r;
+  return LBM_OK;
+}
+
+int lbm_shape_info(int lattice, int prec, int index, int* stage, int* block) {
+  if (lattice != LBM_D2Q37 && lattice != LBM_D3Q107) return fail(LBM_EINVAL, "unknown lattice");
+  if (prec < kF64 || prec > kF32S16BF) return fail(LBM_EINVAL, "unknown precision");
+  const Launchers& L = launchers_for(lattice, prec);
+  if (index < 0 || index >= L.shape_count()) return fail(LBM_EINVAL, "shape index out of range");
+  int st = 0, bx = 0;
+  L.shape_get(index, &st, &bx);
+  if (stage) *stage = st;
+  if (block) *block = bx;
+  return LBM_OK;
+}
+
+int lbm_set_shape(lbm_handle h, int index) {
+  if (!h) return fail(LBM_EINVAL, "handle is NULL");
+  if (index < 0 || index >= launchers_of(h).shape_count()) return fail(LBM_EINVAL, "shape index out of range");
+  h->shape.index = index;
+  return LBM_OK;
+}
+
+int lbm_get_shape(lbm_handle h) { return h ? h->shape.index : -1; }
+
+int lbm_autotune(lbm_handle h, int reps, int* best_index, double* best_us) {
+  if (!h) return fail(LBM_EINVAL, "handle is NULL");
+  if (reps < 1) return fail(LBM_EINVAL, "reps must be >= 1");
+  if (h->N == 0) {
+    if (best_index) *best_index = h->shape.index;
+    if (best_us) *best_us = 0.0;
+    return LBM_OK;
+  }
+  // every trial reads the current buffer and writes the idle one without
+  // swapping them, so the state is not changed
+  const int n = launchers_of(h).shape_count();
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "creating tuning events");
+  const int keep = h->shape.index;
+  int best = keep;
+  float best_ms = 0.f;
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    h->shape.index = k;
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_step(h, h->buf[h->cur], h->buf[1 - h->cur]);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_step(h, h->buf[h->cur], h->buf[1 - h->cur]);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (k == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    h->shape.index = keep;
+    return cuda_fail(e, "autotuning the step");
+  }
+  h->shape.index = best;
+  if (best_index) *best_index = best;
+  if (best_us) *best_us = 1e3 * best_ms / reps;
   return LBM_OK;
 }
 

@@ -19,8 +19,7 @@ enum Prec { kF64 = 0, kF32 = 1, kF32S16F = 2, kF32S16BF = 3 };
 // Kernel launch shape of the step, per (lattice, precision); chosen by the
 // built-in defaults or the autotuner.
 struct StepShape {
-  int bx;     // cells per block along x
-  int stage;  // 0 registers, 1 cp.async shared staging, 2 plain shared staging
+  int index;  // candidate index of the (lattice, storage) shape table (launch_impl.cuh)
 };
 
 struct Instance {
@@ -73,6 +72,8 @@ struct Launchers {
   cudaError_t (*pool_advance)(const PoolLaunch& pl);
   int (*pool_grid)();
   int pool_tile_cells;  // cells per tile along x
+  int (*shape_count)();
+  void (*shape_get)(int k, int* stage, int* bx);
 };
 
 extern const Launchers kLaunchers_0_0, kLaunchers_0_1, kLaunchers_0_2, kLaunchers_0_3;

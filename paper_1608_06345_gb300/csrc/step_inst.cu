@@ -39,6 +39,8 @@ extern const Launchers LBM_CAT(kLaunchers, LBM_LAT, LBM_PREC) = {
     &launch_pool_advance_t<ComputeT>,
     &pool_grid_t<LBM_LAT, StoreT, ComputeT>,
     pool_tile_cells<LBM_LAT, StoreT>(),
+    &shape_count_t<LBM_LAT, StoreT>,
+    &shape_get_t<LBM_LAT, StoreT>,
 };
 
 }  // namespace lbm

@@ -33,7 +33,8 @@ EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init
            "lbm_raw_state_bytes", "lbm_get_state", "lbm_set_state", "lbm_lattice_table", "lbm_last_error",
            "lbm_conserved_noalloc", "lbm_pool_bytes", "lbm_pool_create", "lbm_pool_destroy",
            "lbm_pool_instance_bytes", "lbm_pool_submit", "lbm_pool_run", "lbm_pool_sync", "lbm_pool_poll",
-           "lbm_pool_result", "lbm_pool_stats"]
+           "lbm_pool_result", "lbm_pool_stats", "lbm_shape_info", "lbm_set_shape", "lbm_get_shape",
+           "lbm_autotune"]
 
 
 class LbmError(RuntimeError):
@@ -96,6 +97,10 @@ def load(build_if_missing: bool = False):
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_conserved_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, vp, ctypes.c_longlong, ctypes.c_longlong, vp, dp]),
+        "lbm_shape_info": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]),
+        "lbm_set_shape": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_get_shape": (ctypes.c_int, [vp]),
+        "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ip, dp]),
         "lbm_pool_bytes": (ctypes.c_size_t, [ctypes.POINTER(lbm_pool_config)]),
         "lbm_pool_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(lbm_pool_config)]),
         "lbm_pool_destroy": (ctypes.c_int, [vp]),
@@ -223,6 +228,28 @@ def lbm_lattice_table(lattice):
                                     w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(r)))
     Q = q.value
     return c[: Q * D].reshape(Q, D).astype(np.int64), w[:Q].copy(), r.value
+
+
+def lbm_shape_info(lattice, prec, index):
+    """(stage, block) of candidate shape `index`, or None past the end."""
+    st, bx = ctypes.c_int(), ctypes.c_int()
+    rc = load().lbm_shape_info(lattice, prec, index, ctypes.byref(st), ctypes.byref(bx))
+    return (st.value, bx.value) if rc == LBM_OK else None
+
+
+def lbm_set_shape(h, index):
+    return _check(load().lbm_set_shape(h, int(index)))
+
+
+def lbm_get_shape(h):
+    return load().lbm_get_shape(h)
+
+
+def lbm_autotune(h, reps=5):
+    """(best shape index, microseconds per step)."""
+    k, us = ctypes.c_int(), ctypes.c_double()
+    _check(load().lbm_autotune(h, int(reps), ctypes.byref(k), ctypes.byref(us)))
+    return k.value, us.value
 
 
 def lbm_conserved_noalloc(lattice, prec, gamma, state, ncells, plane_stride, stream=None, rho0=0.0, T0=0.0):
