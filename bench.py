@@ -35,6 +35,14 @@ import lbm_inputs as li  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
 
+# FP64 paths are bound by GB300's FP64 pipe, not by HBM.  Peak: 152 SMs x 2
+# FP64 instructions per clock x 2 flop (FMA) x 2.07 GHz = 1.259 TFLOP/s
+# (the GPU's nominal 1.25 TFLOP/s FP64 rate).  Flops per cell update of the
+# D2Q37 FP64 step from ncu's SASS counters (profiles/step_d2q37_f64.md):
+# 299 DFMA + 175 DADD + 95 DMUL per cell = 868 flop.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+FP64_FLOPS_PER_CELL = {0: 868}
+
 WORKLOADS = {
     # name: lattice, prec, shape, gamma, tau_f, tau_g, steps per solve, fields
     "periodic2d": dict(lattice=0, prec="f32", shape=(4096, 4096), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=200,
@@ -50,6 +58,10 @@ WORKLOADS = {
     "periodic2d_s16bf": dict(lattice=0, prec="f32_s16bf", shape=(4096, 4096), gamma=1.4, tau_f=0.55, tau_g=0.7,
                              steps=200, fields="fourier2d",
                              desc="D2Q37 FP32 compute, BF16 deviation storage, periodic 4096x4096, 200 steps"),
+    "sod2d": dict(lattice=0, prec="f64", shape=(1000, 4), bc=(1, 0), gamma=1.4, tau_f=0.6, tau_g=0.6, steps=500,
+                  fields="sod",
+                  desc="D2Q37 FP64 Sod shock tube 1000x4 (rho 1|0.125, p 1|0.1, zero-gradient x, periodic y), "
+                       "gamma 1.4, tau 0.6, 500 steps per solve"),
     "periodic2d_small": dict(lattice=0, prec="f32", shape=(1024, 1024), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=20,
                              fields="fourier2d",
                              desc="D2Q37 FP32 periodic 1024x1024 (profiling case, 0.6 GB state > L2), 20 steps"),
@@ -75,6 +87,18 @@ def dist_info():
 
 
 def make_fields(wl, shape):
+    if wl["prec"] == "f64" and wl["lattice"] in FP64_FLOPS_PER_CELL:
+        # the FP64 step is ALU-bound: report it against the FP64 pipe
+        fl = FP64_FLOPS_PER_CELL[wl["lattice"]]
+        hbm = line["roofline"]
+        line["roofline"] = {"bound": "alu", "achieved": fl * cells_per_s / 1e9, "peak": FP64_PEAK_GFLOPS,
+                            "unit": "GFLOP/s", "frac": fl * cells_per_s / 1e9 / FP64_PEAK_GFLOPS,
+                            "traffic": hbm["traffic"], "kernel": hbm["kernel"], "flops_per_cell_update": fl,
+                            "peak_kind": "derived: 152 SMs x 2 FP64 inst/clk x 2 flop x 2.07 GHz",
+                            "step_kernel_us": hbm["step_kernel_us"], "hbm_achieved_gbs": hbm["achieved"],
+                            "hbm_frac": hbm["frac"], "shape": hbm["shape"]}
+    if wl["fields"] == "sod":
+        return li.sod_fields(shape[0], shape[1])
     if wl["fields"] == "fourier2d":
         return li.fourier_fields(shape, seed_u=1, seed_rho=2)
     if wl["fields"] == "fourier3d":
@@ -244,7 +268,8 @@ def run_ours(args, wl):
     rho, u, T = make_fields(wl, shape)
 
     stream = torch.cuda.current_stream()
-    solver = lbm.Solver(wl["lattice"], wl["gamma"], wl["tau_f"], wl["tau_g"], shape, prec=prec, stream=stream)
+    solver = lbm.Solver(wl["lattice"], wl["gamma"], wl["tau_f"], wl["tau_g"], shape, bc=wl.get("bc", (0, 0, 0)),
+                        prec=prec, stream=stream)
     d_rho = torch.from_numpy(rho).to(device)
     d_u = torch.from_numpy(np.ascontiguousarray(u)).to(device)
     d_T = torch.from_numpy(T).to(device)
@@ -336,6 +361,7 @@ def run_ours(args, wl):
         return
 
     word = {"f64": 8, "f32": 4, "f32_s16f": 2, "f32_s16bf": 2}[wl["prec"]]
+    cells_per_s = N / step_kernel_s
     Q = 37 if wl["lattice"] == 0 else 107
     bytes_per_cell = 2 * Q * 2 * word
     peak, peak_kind = measured_peaks()
@@ -369,6 +395,31 @@ def run_ours(args, wl):
         "clocks": clk,
         "cpu_baseline": cpu,
     }
+    if wl["prec"] == "f64" and wl["lattice"] in FP64_FLOPS_PER_CELL:
+        # the FP64 step is ALU-bound: report it against the FP64 pipe
+        fl = FP64_FLOPS_PER_CELL[wl["lattice"]]
+        hbm = line["roofline"]
+        line["roofline"] = {"bound": "alu", "achieved": fl * cells_per_s / 1e9, "peak": FP64_PEAK_GFLOPS,
+                            "unit": "GFLOP/s", "frac": fl * cells_per_s / 1e9 / FP64_PEAK_GFLOPS,
+                            "traffic": hbm["traffic"], "kernel": hbm["kernel"], "flops_per_cell_update": fl,
+                            "peak_kind": "derived: 152 SMs x 2 FP64 inst/clk x 2 flop x 2.07 GHz",
+                            "step_kernel_us": hbm["step_kernel_us"], "hbm_achieved_gbs": hbm["achieved"],
+                            "hbm_frac": hbm["frac"], "shape": hbm["shape"]}
+    if wl["fields"] == "sod":
+        # accuracy of the last solve against the exact Riemann solution (cells
+        # 0..nx/2: the shock has left the tube by step 500, the rarefaction not)
+        from oracle import riemann
+        rg, Tg = o_rho.cpu().numpy(), o_T.cpu().numpy()
+        ug = o_u.cpu().numpy().reshape(D, -1)[0]
+        _, _, rr = lbm.lbm_lattice_table(0)
+        t = riemann.lattice_time(S, shape[0], rr)
+        er, eu, eT = riemann.shock_tube_profile((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, shape[0], t)
+        half = slice(0, shape[0] // 2)
+        line["accuracy_vs_exact"] = {
+            "t": t, "cells": "0..nx/2 of row 0",
+            "l1_rho": riemann.l1_error(rg[: shape[0]], er, half), "l1_u": riemann.l1_error(ug[: shape[0]], eu, half),
+            "l1_T": riemann.l1_error(Tg[: shape[0]], eT, half)}
+        line["us_per_lattice_step"] = elapsed / (args.steps * S) * 1e6
     if world == 1 and args.workload == "periodic2d" and not args.no_serving:
         line["serving"] = serving_eval(args)
     print(json.dumps(line), flush=True)
@@ -412,7 +463,9 @@ def serving_eval(args):
         loads.append(s)
 
     def make_solver(req):
-        return lbm.Solver(0, req.gamma, req.tau_f, req.tau_g, req.shape, bc=req.bc, prec=lbm.LBM_F64)
+        s = lbm.Solver(0, req.gamma, req.tau_f, req.tau_g, req.shape, bc=req.bc, prec=lbm.LBM_F64)
+        lbm.lbm_set_graph_steps(s.h, 0)  # the plain method: one launch per step
+        return s
 
     base = None
     if not args.no_baseline:

@@ -103,8 +103,14 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T);
 int lbm_init_device(lbm_handle h, const double* rho, const double* u, const double* T);
 
 /* Advance n >= 0 time steps (pull-stream + BGK collide of g and h per step).
- * Asynchronous on the instance's stream. */
+ * Asynchronous on the instance's stream.  Runs of at least twice the graph
+ * length (lbm_set_graph_steps, default 64) replay a captured CUDA graph of
+ * that many steps instead of launching each step; the arithmetic is the same. */
 int lbm_step(lbm_handle h, long n);
+
+/* Steps per CUDA graph replay of lbm_step (even, 0..4096); 0 launches every
+ * step separately (the plain one-launch-per-step path). */
+int lbm_set_graph_steps(lbm_handle h, int steps);
 
 /* rho, u, T of the stored (post-collision) state, Eq. (14)/(15), into host
  * arrays of N, D*N, N doubles.  Synchronises; returns LBM_ENONFINITE if any

@@ -20,7 +20,8 @@ constexpr size_t step_smem() {
 }
 
 template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1>
-cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, const Args<C>& a) {
+cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, const Args<C>& a,
+                          bool configure_only = false) {
   const dim3 grid((unsigned)((inst->n[0] + BX - 1) / BX), (unsigned)inst->n[1], (unsigned)inst->n[2]);
   size_t smem = 0;
   if constexpr (STAGE != 0) {
@@ -38,6 +39,7 @@ cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, cons
       if (dev < 64) configured |= (1ull << dev);
     }
   }
+  if (configure_only) return cudaSuccess;
   k_step<LAT, S, C, STAGE, BX, MINB><<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst),
                                                                   a);
   return cudaGetLastError();
@@ -79,38 +81,50 @@ void shape_get_t(int k, int* stage, int* bx) {
 }
 
 template <int LAT, class S, class C>
-cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst) {
+cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, bool configure_only = false) {
   const Args<C>& a = args_of<C>(inst);
   const int k = inst->shape.index;
   if constexpr (LAT == 0 && sizeof(S) == 8) {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 0, 256>(inst, src, dst, a);
-      case 2: return launch_step_t<LAT, S, C, 0, 64>(inst, src, dst, a);
-      default: return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a);
+      case 1: return launch_step_t<LAT, S, C, 0, 256>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_t<LAT, S, C, 0, 64>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (LAT == 0) {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 0, 256, 2>(inst, src, dst, a);
-      case 2: return launch_step_t<LAT, S, C, 0, 64, 8>(inst, src, dst, a);
-      case 3: return launch_step_t<LAT, S, C, 0, 128, 1>(inst, src, dst, a);
-      default: return launch_step_t<LAT, S, C, 0, 128, 4>(inst, src, dst, a);
+      case 1: return launch_step_t<LAT, S, C, 0, 256, 2>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_t<LAT, S, C, 0, 64, 8>(inst, src, dst, a, configure_only);
+      case 3: return launch_step_t<LAT, S, C, 0, 128, 1>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 0, 128, 4>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (sizeof(S) == 4) {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 3, 64>(inst, src, dst, a);
-      case 2: return launch_step_t<LAT, S, C, 3, 64, 5>(inst, src, dst, a);
-      case 3: return launch_step_t<LAT, S, C, 3, 64, 6>(inst, src, dst, a);
-      case 4: return launch_step_t<LAT, S, C, 3, 128, 3>(inst, src, dst, a);
-      default: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a);
+      case 1: return launch_step_t<LAT, S, C, 3, 64>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_t<LAT, S, C, 3, 64, 5>(inst, src, dst, a, configure_only);
+      case 3: return launch_step_t<LAT, S, C, 3, 64, 6>(inst, src, dst, a, configure_only);
+      case 4: return launch_step_t<LAT, S, C, 3, 128, 3>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (sizeof(S) == 8) {
-    return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a);
+    return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
   } else {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 2, 32>(inst, src, dst, a);
-      default: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a);
+      case 1: return launch_step_t<LAT, S, C, 2, 32>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a, configure_only);
     }
   }
+}
+
+// sets the shape's kernel attributes on the current device without
+// launching (done before a graph capture)
+template <int LAT, class S, class C>
+cudaError_t configure_step_t(const Instance* inst) {
+  return launch_step_shape<LAT, S, C>(inst, nullptr, nullptr, true);
+}
+
+template <int LAT, class S, class C>
+cudaError_t launch_step_plain(const Instance* inst, const void* src, void* dst) {
+  return launch_step_shape<LAT, S, C>(inst, src, dst, false);
 }
 
 // pool: the shape of the batched step per (lattice, storage)

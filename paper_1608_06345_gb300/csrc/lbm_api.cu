@@ -192,6 +192,10 @@ int prepare_instance(Instance* I, int lattice, double gamma, double tau_f, doubl
   I->rho0 = grid->rho0 > 0.0 ? grid->rho0 : 1.0;
   I->T0 = grid->T0 > 0.0 ? grid->T0 : 1.0;
   I->shape = default_shape(lattice, grid->prec);
+  I->graph_steps = 64;
+  I->graph_shape = -1;
+  I->graph_exec = nullptr;
+  I->graph = nullptr;
   if (build_lattice_table(lattice, &I->table) != 0) return fail(LBM_EINVAL, "lattice table refinement failed");
   I->G = I->table.G;
   return LBM_OK;
@@ -208,6 +212,51 @@ const Launchers& launchers_for(int lattice, int prec) {
   static const Launchers* table[2][4] = {{&kLaunchers_0_0, &kLaunchers_0_1, &kLaunchers_0_2, &kLaunchers_0_3},
                                          {&kLaunchers_1_0, &kLaunchers_1_1, &kLaunchers_1_2, &kLaunchers_1_3}};
   return *table[lattice][prec];
+}
+
+void drop_graph(Instance* I) {
+  if (I->graph_exec) cudaGraphExecDestroy(I->graph_exec);
+  if (I->graph) cudaGraphDestroy(I->graph);
+  I->graph_exec = nullptr;
+  I->graph = nullptr;
+  I->graph_shape = -1;
+}
+
+// Capture graph_steps steps starting from buffer cur (on a private stream:
+// the legacy default stream cannot be captured); the instance's stream
+// then replays it.
+cudaError_t capture_graph(Instance* I) {
+  drop_graph(I);
+  cudaError_t e = launchers_of(I).configure(I);
+  if (e != cudaSuccess) return e;
+  cudaStream_t cs;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaStream_t keep = I->stream;
+  I->stream = cs;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  cudaError_t le = cudaSuccess;
+  if (e == cudaSuccess) {
+    int c = I->cur;
+    for (int k = 0; k < I->graph_steps && le == cudaSuccess; ++k) {
+      le = launch_step(I, I->buf[c], I->buf[1 - c]);
+      c ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess && le == cudaSuccess) {
+      e = cudaGraphInstantiate(&I->graph_exec, g, 0);
+      if (e == cudaSuccess) I->graph = g;
+      else cudaGraphDestroy(g);
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+  }
+  I->stream = keep;
+  cudaStreamDestroy(cs);
+  if (le != cudaSuccess) return le;
+  if (e == cudaSuccess) I->graph_shape = I->shape.index;
+  return e;
 }
 
 }  // namespace lbm
@@ -280,6 +329,10 @@ int lbm_destroy(lbm_handle h) {
   if (!h) return LBM_OK;
   lbm_instance* I = h;
   int rc = LBM_OK;
+  if (I->graph_exec) {
+    cudaStreamSynchronize(I->stream);
+    drop_graph(I);
+  }
   if (I->own_mem) {
     cudaError_t e = cudaStreamSynchronize(I->stream);
     if (e == cudaSuccess) e = cudaFree(I->mem);
@@ -320,6 +373,31 @@ int lbm_step(lbm_handle h, long n) {
   if (!h) return fail(LBM_EINVAL, "handle is NULL");
   if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
   if (h->N == 0) return LBM_OK;
+  // whole bundles as graph replays (the graph's even step count leaves cur
+  // unchanged; it is captured from the current parity, so recapture if the
+  // shape changed), the remainder as plain launches
+  if (h->graph_steps > 0 && n >= 2L * h->graph_steps) {
+    if (!h->graph_exec || h->graph_shape != h->shape.index || h->cur != 0) {
+      // the graph is captured with buffer 0 current: step once if needed
+      if (h->cur != 0) {
+        cudaError_t e = launch_step(h, h->buf[h->cur], h->buf[1 - h->cur]);
+        if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
+        h->cur ^= 1;
+        ++h->steps_done;
+        --n;
+      }
+      if (!h->graph_exec || h->graph_shape != h->shape.index) {
+        cudaError_t e = capture_graph(h);
+        if (e != cudaSuccess) return cuda_fail(e, "capturing the step graph");
+      }
+    }
+    while (n >= h->graph_steps) {
+      cudaError_t e = cudaGraphLaunch(h->graph_exec, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "launching the step graph");
+      n -= h->graph_steps;
+      h->steps_done += h->graph_steps;
+    }
+  }
   for (long k = 0; k < n; ++k) {
     cudaError_t e = launch_step(h, h->buf[h->cur], h->buf[1 - h->cur]);
     if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
@@ -449,6 +527,17 @@ int lbm_set_shape(lbm_handle h, int index) {
 }
 
 int lbm_get_shape(lbm_handle h) { return h ? h->shape.index : -1; }
+
+int lbm_set_graph_steps(lbm_handle h, int steps) {
+  if (!h) return fail(LBM_EINVAL, "handle is NULL");
+  if (steps < 0 || steps % 2 != 0 || steps > 4096) return fail(LBM_EINVAL, "graph steps must be even, 0..4096");
+  if (steps != h->graph_steps) {
+    cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    h->graph_steps = steps;
+  }
+  return LBM_OK;
+}
 
 int lbm_autotune(lbm_handle h, int reps, int* best_index, double* best_us) {
   if (!h) return fail(LBM_EINVAL, "handle is NULL");

@@ -43,6 +43,12 @@ struct Instance {
   Args<double> ad;
   Args<float> af;
   StepShape shape;
+  // CUDA graph of `graph_steps` consecutive steps (even, so the buffers are
+  // back in place after a replay); 0 = plain launches
+  int graph_steps;
+  int graph_shape;           // shape index the graph was captured with
+  cudaGraphExec_t graph_exec;
+  cudaGraph_t graph;
 };
 
 // Bytes of the tail region after the two buffers.
@@ -74,6 +80,7 @@ struct Launchers {
   int pool_tile_cells;  // cells per tile along x
   int (*shape_count)();
   void (*shape_get)(int k, int* stage, int* bx);
+  cudaError_t (*configure)(const Instance* inst);
 };
 
 extern const Launchers kLaunchers_0_0, kLaunchers_0_1, kLaunchers_0_2, kLaunchers_0_3;

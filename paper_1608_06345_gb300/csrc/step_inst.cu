@@ -31,7 +31,7 @@ using ComputeT = float;
 #define LBM_CAT(a, b, c) LBM_CAT2(a, b, c)
 
 extern const Launchers LBM_CAT(kLaunchers, LBM_LAT, LBM_PREC) = {
-    &launch_step_shape<LBM_LAT, StoreT, ComputeT>,
+    &launch_step_plain<LBM_LAT, StoreT, ComputeT>,
     &launch_init_t<LBM_LAT, StoreT, ComputeT>,
     &launch_moments_t<LBM_LAT, StoreT, ComputeT>,
     &launch_conserve_t<LBM_LAT, StoreT>,
@@ -41,6 +41,7 @@ extern const Launchers LBM_CAT(kLaunchers, LBM_LAT, LBM_PREC) = {
     pool_tile_cells<LBM_LAT, StoreT>(),
     &shape_count_t<LBM_LAT, StoreT>,
     &shape_get_t<LBM_LAT, StoreT>,
+    &configure_step_t<LBM_LAT, StoreT, ComputeT>,
 };
 
 }  // namespace lbm

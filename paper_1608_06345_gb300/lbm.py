@@ -34,7 +34,7 @@ EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init
            "lbm_conserved_noalloc", "lbm_pool_bytes", "lbm_pool_create", "lbm_pool_destroy",
            "lbm_pool_instance_bytes", "lbm_pool_submit", "lbm_pool_run", "lbm_pool_sync", "lbm_pool_poll",
            "lbm_pool_result", "lbm_pool_stats", "lbm_shape_info", "lbm_set_shape", "lbm_get_shape",
-           "lbm_autotune"]
+           "lbm_autotune", "lbm_set_graph_steps"]
 
 
 class LbmError(RuntimeError):
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = False):
         "lbm_set_shape": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_get_shape": (ctypes.c_int, [vp]),
         "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ip, dp]),
+        "lbm_set_graph_steps": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_pool_bytes": (ctypes.c_size_t, [ctypes.POINTER(lbm_pool_config)]),
         "lbm_pool_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(lbm_pool_config)]),
         "lbm_pool_destroy": (ctypes.c_int, [vp]),
@@ -243,6 +244,10 @@ def lbm_set_shape(h, index):
 
 def lbm_get_shape(h):
     return load().lbm_get_shape(h)
+
+
+def lbm_set_graph_steps(h, steps):
+    return _check(load().lbm_set_graph_steps(h, int(steps)))
 
 
 def lbm_autotune(h, reps=5):

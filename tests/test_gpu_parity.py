@@ -204,3 +204,25 @@ def test_checkpoint_roundtrip():
     rb = b.moments()
     for qa, qb in zip(ra, rb):
         assert np.array_equal(qa, qb)
+
+
+@pytest.mark.parametrize("lat,shape,prec", [(0, (150, 6), F64), (1, (40, 5, 4), F32)])
+def test_graph_replay_equals_plain_launches(lat, shape, prec):
+    """lbm_step replays captured graphs for long runs; the result is bitwise
+    that of one launch per step, also when a run starts on the odd buffer."""
+    from paper_1608_06345_gb300 import lbm
+    D = len(shape)
+    fields = fields_for(shape, seed=23)
+    out = []
+    for gsteps in (0, 8):
+        s = lbm.Solver(lat, 1.4, 0.6, 0.7, shape, prec=prec)
+        lbm.lbm_set_graph_steps(s.h, gsteps)
+        s.init(*fields)
+        s.step(1)      # odd parity before the long run
+        s.step(37)     # >= 2 graphs + remainder
+        s.step(16)
+        assert lbm.lbm_steps_done(s.h) == 54
+        out.append(s.moments())
+        s.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
