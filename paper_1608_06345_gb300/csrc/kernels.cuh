@@ -267,26 +267,61 @@ __device__ __forceinline__ int pull_coord(int p, int c, int n, int bc) {
 //   T = (2E - u^2)/(D + delta) = T0 + dT,
 //   dT = [2 (dK + dH) - rho u^2 - (D + delta) T0 drho] / (rho (D + delta))
 // ---------------------------------------------------------------------------
-template <int LAT, class C, class GetG, class GetH>
-__device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args<C>& a, C& drho, C (&u)[3],
+// SCALED: the accessors return the stored 16-bit values d, e (dg = gref d,
+// dh = hscale e); the group scales are folded into the sums' coefficients
+// instead of decoding every value.
+template <int LAT, class C, bool SCALED, class GetG, class GetH>
+__device__ __forceinline__ void moments_raw(GetG&& getg, GetH&& geth, const Args<C>& a, C& drho, C (&u)[3],
                                             C& dT) {
   using L = Lat<LAT>;
-  C m = getg(std::integral_constant<int, 0>{});
-  C H = geth(std::integral_constant<int, 0>{});
+  C m, H;
+  if constexpr (SCALED) {
+    m = a.gref[0] * getg(std::integral_constant<int, 0>{});
+    H = a.hscale[0] * geth(std::integral_constant<int, 0>{});
+  } else {
+    m = getg(std::integral_constant<int, 0>{});
+    H = geth(std::integral_constant<int, 0>{});
+  }
   C jx = C(0), jy = C(0), jz = C(0), k2 = C(0);
+  C s1 = C(1), s2 = C(2), s3 = C(3), sc2 = C(0), sh = C(1);  // group scale times 1, 2, 3, |c|^2; h scale
   static_for<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if constexpr (i % 2 == 1) {
+      constexpr int g = L::grp(i);
+      if constexpr (SCALED && L::grp(i - 1) != g) {
+        s1 = a.gref[g];
+        s2 = C(2) * s1;
+        s3 = C(3) * s1;
+        sc2 = C(L::c2(i)) * s1;
+        sh = a.hscale[g];
+      }
+      auto mul = [&](int c) -> C {  // the coefficient c * scale for |c| <= 3
+        const int ac = c < 0 ? -c : c;
+        const C v = ac == 1 ? s1 : (ac == 2 ? s2 : s3);
+        return c < 0 ? -v : v;
+      };
       const C gp = getg(I), gm = getg(std::integral_constant<int, i + 1>{});
       const C sp = gp + gm, df = gp - gm;
-      m += sp;
-      if constexpr (L::cx(i) != 0) jx = fma(C(L::cx(i)), df, jx);
-      if constexpr (L::cy(i) != 0) jy = fma(C(L::cy(i)), df, jy);
-      if constexpr (L::cz(i) != 0) jz = fma(C(L::cz(i)), df, jz);
-      k2 = fma(C(L::c2(i)), sp, k2);
-      H += geth(I) + geth(std::integral_constant<int, i + 1>{});
+      const C hp = geth(I) + geth(std::integral_constant<int, i + 1>{});
+      if constexpr (SCALED) {
+        m = fma(s1, sp, m);
+        if constexpr (L::cx(i) != 0) jx = fma(mul(L::cx(i)), df, jx);
+        if constexpr (L::cy(i) != 0) jy = fma(mul(L::cy(i)), df, jy);
+        if constexpr (L::cz(i) != 0) jz = fma(mul(L::cz(i)), df, jz);
+        k2 = fma(sc2, sp, k2);
+        H = fma(sh, hp, H);
+      } else {
+        m += sp;
+        if constexpr (L::cx(i) != 0) jx = fma(C(L::cx(i)), df, jx);
+        if constexpr (L::cy(i) != 0) jy = fma(C(L::cy(i)), df, jy);
+        if constexpr (L::cz(i) != 0) jz = fma(C(L::cz(i)), df, jz);
+        k2 = fma(C(L::c2(i)), sp, k2);
+        H += hp;
+      }
     }
   });
+  (void)s2;
+  (void)s3;
   const C rho = a.rho0 + m;
   const C inv = C(1) / rho;
   drho = m;
@@ -298,33 +333,72 @@ __device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args
   dT = (dE2 - rho * u2 - a.Dd * a.T0 * m) * inv * a.inv_Dd;
 }
 
+template <int LAT, class C, class GetG, class GetH>
+__device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args<C>& a, C& drho, C (&u)[3],
+                                            C& dT) {
+  moments_raw<LAT, C, false>(getg, geth, a, drho, u, dT);
+}
+
 // ---------------------------------------------------------------------------
 // collide one cell given its pulled deviations and store the result:
 //   g* = g~ + omega_f (dF - g~)
 //   h* = h~ + omega_g (dFh - h~) = (omega_g hd T) dF + (1 - omega_g) h~ + omega_g hd dT gref
 // ---------------------------------------------------------------------------
-template <int LAT, class S, class C, class GetG, class GetH>
+// For 16-bit storage the accessors return the stored d, e and the new values
+// are formed directly in the stored scale:
+//   d* = d + omega_f (dF / gref - d),  e* = (hA / hs) dF + (1 - omega_g) e + hb gref / hs
+template <int LAT, class S, class C, bool IDX32, class GetG, class GetH>
 __device__ __forceinline__ void collide_store(GetG&& getg, GetH&& geth, const Args<C>& a, S* __restrict__ dst,
                                               long long ps, unsigned cell) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
+  constexpr bool SCALED = IsS16<S>::value;
+  // IDX32: element index plane * ps + cell in 32 bits (the caller checked
+  // that 2Q ps < 2^31); else plane base + the cell's byte offset in 64 bits
+  char* db = reinterpret_cast<char*>(dst) + (size_t)cell * sizeof(S);
+  const size_t pb = (size_t)ps * sizeof(S);
+  auto st = [&](int plane, S v) {
+    if constexpr (IDX32) dst[(unsigned)plane * (unsigned)ps + cell] = v;
+    else *reinterpret_cast<S*>(db + (size_t)plane * pb) = v;
+  };
   C drho, u[3], dT;
-  moments_dev<LAT, C>(getg, geth, a, drho, u, dT);
+  moments_raw<LAT, C, SCALED>(getg, geth, a, drho, u, dT);
   if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
   EqCoef<LAT, C> k;
   eq_coeffs<LAT, C>(drho, u, dT, a, k);
   const C hA = a.omega_g * a.half_delta * k.T;
   const C om1 = C(1) - a.omega_g;
   const C hbs = a.omega_g * a.half_delta * dT;
+  C ig = C(1), hAs = hA, hbg = C(0);  // per-group: 1/gref, hA/hs, hbs gref/hs (16-bit)
   eq_emit<LAT, C>(k, a, [&](auto I, C dF) {
     constexpr int i = decltype(I)::value;
     constexpr int g = L::grp(i);
     const C gi = getg(I), hi = geth(I);
-    const C gn = fma(a.omega_f, dF - gi, gi);
-    const C hn = fma(hA, dF, fma(om1, hi, hbs * a.gref[g]));
-    dst[i * ps + cell] = encode<S, C, false>(gn, g, a);
-    dst[(Q + i) * ps + cell] = encode<S, C, true>(hn, g, a);
+    if constexpr (SCALED) {
+      if constexpr (i == 0 || L::grp(i == 0 ? 0 : i - 1) != g) {
+        ig = a.inv_gref[g];
+        hAs = hA * a.inv_hscale[g];
+        hbg = hbs * a.gref[g] * a.inv_hscale[g];
+      }
+      const C dn = fma(a.omega_f, fma(dF, ig, -gi), gi);
+      const C en = fma(hAs, dF, fma(om1, hi, hbg));
+      st(i, f_to_s16<S>(static_cast<float>(dn)));
+      st(Q + i, f_to_s16<S>(static_cast<float>(en)));
+    } else {
+      const C gn = fma(a.omega_f, dF - gi, gi);
+      const C hn = fma(hA, dF, fma(om1, hi, hbs * a.gref[g]));
+      st(i, static_cast<S>(gn));
+      st(Q + i, static_cast<S>(hn));
+    }
   });
+}
+
+// raw value of a stored population in the compute type (16-bit: the stored
+// relative deviation, not decoded)
+template <class S, class C>
+__device__ __forceinline__ C raw_value(S v) {
+  if constexpr (IsS16<S>::value) return static_cast<C>(s16_to_f(v));
+  else return static_cast<C>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,7 +411,7 @@ __device__ __forceinline__ void collide_store(GetG&& getg, GetH&& geth, const Ar
 //            FP32/FP64): half the shared memory per cell of STAGE 1
 // A block covers BX consecutive cells of a row (thread = cell).
 // ---------------------------------------------------------------------------
-template <int LAT, class S, class C, int STAGE, int BX>
+template <int LAT, class S, class C, int STAGE, int BX, bool IDX32 = false>
 __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restrict__ dst, const Args<C>& a, int x,
                                           int y, int z) {
   using L = Lat<LAT>;
@@ -358,16 +432,28 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     constexpr int i = decltype(I)::value;
     return zo[L::cz(i) + 3] + yo[L::cy(i) + 3] + xo[L::cx(i) + 3];
   };
-
+  // addresses = plane base (uniform across the grid) + per-thread byte
+  // offset; g_i and h_i share the offset of direction i
+  const char* sb = reinterpret_cast<const char*>(src);
+  const size_t pb = (size_t)ps * sizeof(S);
+  auto ld = [&](auto I, int plane, size_t offb) -> S {
+    return ldg_s(reinterpret_cast<const S*>(sb + (size_t)plane * pb + offb));
+  };
   if constexpr (STAGE == 0) {
     C g[Q], h[Q];
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const unsigned off = src_off(I);
-      g[i] = decode<S, C, false>(ldg_s(src + i * ps + off), L::grp(i), a);
-      h[i] = decode<S, C, true>(ldg_s(src + (Q + i) * ps + off), L::grp(i), a);
+      if constexpr (IDX32) {
+        const unsigned off = src_off(I);
+        g[i] = raw_value<S, C>(ldg_s(src + ((unsigned)i * (unsigned)ps + off)));
+        h[i] = raw_value<S, C>(ldg_s(src + ((unsigned)(Q + i) * (unsigned)ps + off)));
+      } else {
+        const size_t offb = (size_t)src_off(I) * sizeof(S);
+        g[i] = raw_value<S, C>(ld(I, i, offb));
+        h[i] = raw_value<S, C>(ld(I, Q + i, offb));
+      }
     });
-    collide_store<LAT, S, C>([&](auto I) { return g[decltype(I)::value]; },
+    collide_store<LAT, S, C, IDX32>([&](auto I) { return g[decltype(I)::value]; },
                              [&](auto I) { return h[decltype(I)::value]; }, a, dst, ps, cell);
   } else if constexpr (STAGE == 3) {
     static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
@@ -377,14 +463,14 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     C g[Q];
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const unsigned off = src_off(I);
+      const size_t offb = (size_t)src_off(I) * sizeof(S);
       const unsigned sa = (unsigned)__cvta_generic_to_shared(sh + i * BX + t);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src + (Q + i) * ps + off),
-                   "n"(sizeof(S)));
-      g[i] = static_cast<C>(ldg_s(src + i * ps + off));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa),
+                   "l"(sb + (size_t)(Q + i) * pb + offb), "n"(sizeof(S)));
+      g[i] = static_cast<C>(ld(I, i, offb));
     });
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    collide_store<LAT, S, C>([&](auto I) { return g[decltype(I)::value]; },
+    collide_store<LAT, S, C, IDX32>([&](auto I) { return g[decltype(I)::value]; },
                              [&](auto I) { return static_cast<C>(sh[decltype(I)::value * BX + t]); }, a, dst, ps,
                              cell);
   } else {
@@ -393,38 +479,31 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     const int t = threadIdx.x;
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const unsigned off = src_off(I);
+      const size_t offb = (size_t)src_off(I) * sizeof(S);
       if constexpr (STAGE == 1) {
         static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
         const unsigned sa0 = (unsigned)__cvta_generic_to_shared(sg + i * BX + t);
         const unsigned sa1 = (unsigned)__cvta_generic_to_shared(sg + (Q + i) * BX + t);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa0), "l"(src + i * ps + off),
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa0), "l"(sb + (size_t)i * pb + offb),
                      "n"(sizeof(S)));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa1), "l"(src + (Q + i) * ps + off),
-                     "n"(sizeof(S)));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa1),
+                     "l"(sb + (size_t)(Q + i) * pb + offb), "n"(sizeof(S)));
       } else {
-        sg[i * BX + t] = ldg_s(src + i * ps + off);
-        sg[(Q + i) * BX + t] = ldg_s(src + (Q + i) * ps + off);
+        sg[i * BX + t] = ld(I, i, offb);
+        sg[(Q + i) * BX + t] = ld(I, Q + i, offb);
       }
     });
     if constexpr (STAGE == 1) asm volatile("cp.async.wait_all;\n" ::: "memory");
     // each thread reads back only the slots it filled itself
-    collide_store<LAT, S, C>(
-        [&](auto I) {
-          constexpr int i = decltype(I)::value;
-          return decode<S, C, false>(sg[i * BX + t], L::grp(i), a);
-        },
-        [&](auto I) {
-          constexpr int i = decltype(I)::value;
-          return decode<S, C, true>(sg[(Q + i) * BX + t], L::grp(i), a);
-        },
-        a, dst, ps, cell);
+    collide_store<LAT, S, C, IDX32>(
+        [&](auto I) { return raw_value<S, C>(sg[decltype(I)::value * BX + t]); },
+        [&](auto I) { return raw_value<S, C>(sg[(Q + decltype(I)::value) * BX + t]); }, a, dst, ps, cell);
   }
 }
 
-template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1>
+template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false>
 __global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
-  step_cell<LAT, S, C, STAGE, BX>(src, dst, a, blockIdx.x * BX + threadIdx.x, blockIdx.y, blockIdx.z);
+  step_cell<LAT, S, C, STAGE, BX, IDX32>(src, dst, a, blockIdx.x * BX + threadIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------

@@ -19,8 +19,8 @@ constexpr size_t step_smem() {
   return STAGE == 0 ? 0 : (STAGE == 3 ? 1 : 2) * sizeof(S) * Lat<LAT>::Q * BX;
 }
 
-template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1>
-cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, const Args<C>& a,
+template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false>
+cudaError_t launch_step_v(const Instance* inst, const void* src, void* dst, const Args<C>& a,
                           bool configure_only = false) {
   const dim3 grid((unsigned)((inst->n[0] + BX - 1) / BX), (unsigned)inst->n[1], (unsigned)inst->n[2]);
   size_t smem = 0;
@@ -33,16 +33,28 @@ cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, cons
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64 || !(configured & (1ull << dev))) {
-      e = cudaFuncSetAttribute(k_step<LAT, S, C, STAGE, BX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = cudaFuncSetAttribute(k_step<LAT, S, C, STAGE, BX, MINB, IDX32>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       if (dev < 64) configured |= (1ull << dev);
     }
   }
   if (configure_only) return cudaSuccess;
-  k_step<LAT, S, C, STAGE, BX, MINB><<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst),
+  k_step<LAT, S, C, STAGE, BX, MINB, IDX32><<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst),
                                                                   a);
   return cudaGetLastError();
+}
+
+// D2Q37 buffers of fewer than 2^31 elements (2Q ps) index in 32 bits, which
+// takes fewer integer instructions per load and store
+template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1>
+cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, const Args<C>& a,
+                          bool configure_only = false) {
+  if constexpr (LAT == 0) {
+    if (2LL * Lat<LAT>::Q * inst->ps < (1LL << 31))
+      return launch_step_v<LAT, S, C, STAGE, BX, MINB, true>(inst, src, dst, a, configure_only);
+  }
+  return launch_step_v<LAT, S, C, STAGE, BX, MINB, false>(inst, src, dst, a, configure_only);
 }
 
 // Candidate shapes of the step per (lattice, storage), tried by the
