@@ -265,6 +265,20 @@ int lbm_pool_result(lbm_pool_handle p, long long ticket, double* rho, double* u,
  * use, arena bytes, work-list entries, persistent grid blocks. */
 int lbm_pool_stats(lbm_pool_handle p, long long* out);
 
+/* General Hermite quadrature (the construction of Sec. IV, for any
+ * symmetric integer velocity set): the velocities are all sign flips and
+ * axis permutations of the ngroups representatives reps[ngroups*D]
+ * (D = 1..3); find one weight per group w_group[ngroups] and the scale r
+ * (xi = r c) such that sum_i w_i (r c_i)^alpha equals the moment E[x^alpha]
+ * of the unit Gaussian for each of the nconds even monomial classes
+ * exps[nconds*D] (odd moments vanish by symmetry).  nconds == ngroups keeps
+ * r = r_in; nconds == ngroups + 1 solves r starting from r_in.  *q gets the
+ * number of velocities, *max_residual the largest relative condition error.
+ * E.g. D2Q9: reps {0,0, 1,0, 1,1}, exps {0,0, 2,0, 4,0, 2,2} -> r = sqrt 3,
+ * w = 4/9, 1/9, 1/36.  LBM_EINVAL with a message if there is no solution. */
+int lbm_quadrature(int D, int ngroups, const int* reps, int nconds, const int* exps, double r_in, int* q,
+                   double* w_group, double* r, double* max_residual);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);
 

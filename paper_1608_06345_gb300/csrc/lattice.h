@@ -102,4 +102,13 @@ struct LatticeTable {
 // Builds the refined table; returns 0 on success.
 int build_lattice_table(int lattice, LatticeTable* out);
 
+// General Hermite quadrature on the integer velocity set spanned by G group
+// representatives (reps[G*D], all sign flips and axis permutations of each):
+// weights per group w[G] and scale r such that sum_i w_i (r c_i)^alpha equals
+// the unit-Gaussian moment for each of the nconds even monomial classes
+// exps[nconds*D].  nconds == G: r = r_in is kept; nconds == G + 1: r is
+// solved from r_in.  Returns 0, or a negative code.
+int hermite_quadrature(int D, int G, const int* reps, int nconds, const int* exps, double r_in, int* Q,
+                       double* w, double* r_out, double* max_residual);
+
 }  // namespace lbm

@@ -11,8 +11,13 @@
 // All conditions but x^8 determine w(r) by a dense solve; r is then the root
 // of the remaining x^8 condition, found by the secant method from [1.19, 1.20]
 // (the printed r is 1.19697977).
+#include <algorithm>
+#include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <vector>
 
 #include "lattice.h"
 
@@ -135,6 +140,147 @@ int build_lattice_table(int lattice, LatticeTable* out) {
     out->x2g[g] = r1 * r1 * L.c2[g];
   }
   for (int g = L.G; g < 10; ++g) out->wg[g] = out->x2g[g] = 0.0;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// General Hermite quadrature on an integer velocity set (the construction the
+// paper applies to D2Q37 and D3Q107, for any symmetric set of groups)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GenSet {
+  int D = 0, G = 0, Q = 0;
+  std::vector<std::array<int, 3>> c;  // velocities
+  std::vector<int> grp;
+};
+
+bool enumerate_set(int D, int G, const int* reps, GenSet* out) {
+  out->D = D;
+  out->G = G;
+  int M = 0;
+  for (int g = 0; g < G; ++g)
+    for (int a = 0; a < D; ++a) M = std::max(M, std::abs(reps[g * D + a]));
+  const int zr = (D == 3) ? M : 0, yr = (D >= 2) ? M : 0;
+  for (int g = 0; g < G; ++g) {
+    int rep[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) rep[a] = std::abs(reps[g * D + a]);
+    std::sort(rep, rep + 3, std::greater<int>());
+    int count = 0;
+    for (int x = -M; x <= M; ++x)
+      for (int y = -yr; y <= yr; ++y)
+        for (int z = -zr; z <= zr; ++z) {
+          int v[3] = {std::abs(x), std::abs(y), std::abs(z)};
+          std::sort(v, v + 3, std::greater<int>());
+          if (v[0] != rep[0] || v[1] != rep[1] || v[2] != rep[2]) continue;
+          out->c.push_back({x, y, z});
+          out->grp.push_back(g);
+          ++count;
+        }
+    if (count == 0) return false;
+  }
+  out->Q = (int)out->c.size();
+  return true;
+}
+
+double gen_group_moment(const GenSet& S, int g, const int* alpha, double r) {
+  double s = 0.0;
+  for (int i = 0; i < S.Q; ++i) {
+    if (S.grp[i] != g) continue;
+    double m = 1.0;
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < alpha[a]; ++k) m *= r * S.c[i][a];
+    s += m;
+  }
+  return s;
+}
+
+// weights for fixed r from all conditions except `drop`; residual of `drop`
+bool gen_weights(const GenSet& S, const std::vector<std::array<int, 3>>& cond, int drop, double r, double* w,
+                 double* resid) {
+  const int G = S.G;
+  std::vector<double> a(G * G), b(G);
+  int row = 0;
+  for (int k = 0; k < (int)cond.size(); ++k) {
+    if (k == drop) continue;
+    for (int g = 0; g < G; ++g) a[row * G + g] = gen_group_moment(S, g, cond[k].data(), r);
+    b[row] = target(cond[k].data());
+    ++row;
+  }
+  if (row != G || !lu_solve(G, a.data(), b.data())) return false;
+  for (int g = 0; g < G; ++g) w[g] = b[g];
+  if (resid) {
+    *resid = 0.0;
+    if (drop >= 0) {
+      double s = 0.0;
+      for (int g = 0; g < G; ++g) s += w[g] * gen_group_moment(S, g, cond[drop].data(), r);
+      *resid = s - target(cond[drop].data());
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+int hermite_quadrature(int D, int G, const int* reps, int nconds, const int* exps, double r_in, int* Q,
+                       double* w, double* r_out, double* max_residual) {
+  if (D < 1 || D > 3 || G < 1 || G > 64 || nconds < 1 || !reps || !exps || !w || !(r_in > 0.0)) return -1;
+  GenSet S;
+  if (!enumerate_set(D, G, reps, &S)) return -2;
+  std::vector<std::array<int, 3>> cond(nconds);
+  for (int k = 0; k < nconds; ++k) {
+    cond[k] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+      if (exps[k * D + a] < 0 || exps[k * D + a] % 2) return -1;  // even moment classes only
+      cond[k][a] = exps[k * D + a];
+    }
+  }
+  double r = r_in;
+  std::vector<double> ww(G);
+  if (nconds == G) {
+    if (!gen_weights(S, cond, -1, r, ww.data(), nullptr)) return -3;
+  } else if (nconds == G + 1) {
+    // r unknown: drop one condition (the highest-degree one that leaves a
+    // regular linear system), solve w(r), and find r by the secant method
+    std::vector<int> order(nconds);
+    for (int k = 0; k < nconds; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+      return cond[p][0] + cond[p][1] + cond[p][2] > cond[q][0] + cond[q][1] + cond[q][2];
+    });
+    bool ok = false;
+    for (int drop : order) {
+      double r0 = r_in * 0.995, r1 = r_in * 1.005, f0, f1;
+      if (!gen_weights(S, cond, drop, r0, ww.data(), &f0) || !gen_weights(S, cond, drop, r1, ww.data(), &f1))
+        continue;
+      for (int it = 0; it < 200 && f1 != f0; ++it) {
+        const double r2 = r1 - f1 * (r1 - r0) / (f1 - f0);
+        if (!(r2 > 0.0)) break;
+        r0 = r1;
+        f0 = f1;
+        r1 = r2;
+        if (!gen_weights(S, cond, drop, r1, ww.data(), &f1)) break;
+        if (std::fabs(r1 - r0) <= 1e-16 * r1) break;
+      }
+      if (gen_weights(S, cond, drop, r1, ww.data(), &f1) && std::fabs(f1) < 1e-9) {
+        r = r1;
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) return -4;
+  } else {
+    return -5;  // need as many conditions as unknowns
+  }
+  double worst = 0.0;
+  for (int k = 0; k < nconds; ++k) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += ww[g] * gen_group_moment(S, g, cond[k].data(), r);
+    worst = std::max(worst, std::fabs(s - target(cond[k].data())) / std::max(1.0, target(cond[k].data())));
+  }
+  for (int g = 0; g < G; ++g) w[g] = ww[g];
+  if (Q) *Q = S.Q;
+  if (r_out) *r_out = r;
+  if (max_residual) *max_residual = worst;
   return 0;
 }
 

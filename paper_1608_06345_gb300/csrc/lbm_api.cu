@@ -583,6 +583,19 @@ int lbm_autotune(lbm_handle h, int reps, int* best_index, double* best_us) {
   return LBM_OK;
 }
 
+int lbm_quadrature(int D, int ngroups, const int* reps, int nconds, const int* exps, double r_in, int* q,
+                   double* w_group, double* r, double* max_residual) {
+  const int rc = hermite_quadrature(D, ngroups, reps, nconds, exps, r_in, q, w_group, r, max_residual);
+  switch (rc) {
+    case 0: return LBM_OK;
+    case -1: return fail(LBM_EINVAL, "invalid arguments (D in 1..3, even exponents, r_in > 0, non-NULL arrays)");
+    case -2: return fail(LBM_EINVAL, "a group representative generates no velocity");
+    case -3: return fail(LBM_EINVAL, "the moment conditions are singular for these groups at r_in");
+    case -4: return fail(LBM_EINVAL, "no scale r satisfies the conditions near r_in");
+    default: return fail(LBM_EINVAL, "need ngroups (r fixed) or ngroups + 1 (r solved) conditions");
+  }
+}
+
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

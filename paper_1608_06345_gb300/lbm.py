@@ -34,7 +34,7 @@ EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init
            "lbm_conserved_noalloc", "lbm_pool_bytes", "lbm_pool_create", "lbm_pool_destroy",
            "lbm_pool_instance_bytes", "lbm_pool_submit", "lbm_pool_run", "lbm_pool_sync", "lbm_pool_poll",
            "lbm_pool_result", "lbm_pool_stats", "lbm_shape_info", "lbm_set_shape", "lbm_get_shape",
-           "lbm_autotune", "lbm_set_graph_steps"]
+           "lbm_autotune", "lbm_set_graph_steps", "lbm_quadrature"]
 
 
 class LbmError(RuntimeError):
@@ -102,6 +102,8 @@ def load(build_if_missing: bool = False):
         "lbm_get_shape": (ctypes.c_int, [vp]),
         "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ip, dp]),
         "lbm_set_graph_steps": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_quadrature": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ip, ctypes.c_double, ip,
+                                          dp, dp, dp]),
         "lbm_pool_bytes": (ctypes.c_size_t, [ctypes.POINTER(lbm_pool_config)]),
         "lbm_pool_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(lbm_pool_config)]),
         "lbm_pool_destroy": (ctypes.c_int, [vp]),
@@ -244,6 +246,22 @@ def lbm_set_shape(h, index):
 
 def lbm_get_shape(h):
     return load().lbm_get_shape(h)
+
+
+def lbm_quadrature(reps, exps, r0=1.0):
+    """General Hermite quadrature: reps (G x D group representatives), exps
+    (n x D even exponents).  Returns (weights per group, r, Q, max residual)."""
+    reps = np.ascontiguousarray(np.asarray(reps, dtype=np.int32))
+    exps = np.ascontiguousarray(np.asarray(exps, dtype=np.int32))
+    G, D = reps.shape
+    n = exps.shape[0]
+    w = np.zeros(G)
+    q, r, res = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(load().lbm_quadrature(D, G, reps.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n,
+                                 exps.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), float(r0), ctypes.byref(q),
+                                 w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(r),
+                                 ctypes.byref(res)))
+    return w, r.value, q.value, res.value
 
 
 def lbm_set_graph_steps(h, steps):

@@ -1,0 +1,68 @@
+"""The paper's own validation runs (Sec. V) at full size on the GPU, against
+the oracle and the exact Riemann solution:
+
+  2D: D2Q37, 1000 x 16, delta = 3 (gamma = 1.4), tau = 2/3, rho 4|1, T 1|1,
+      open x ends, periodic y, 180 steps (t = 0.1504) -- also covered at 500
+      steps by test_gpu_parity.py;
+  3D: D3Q107, 1000 x 16 x 16, delta = 2 (gamma = 1.4), same states, 180 steps;
+  plus a sweep of gamma through delta on the 2D tube (gamma 1.1, 1.3, 5/3, 2:
+  delta = 16, 14/3, 1, 0).
+
+The tubes are uniform across the tube, so the GPU state stays exactly
+uniform in y and z and a 1000 x 1 (x 1) oracle run is the same computation
+per cell.  Parity uses the conditioned tolerance of tests/parity.py; the
+L1 errors against the exact solution must be small (the paper's figure,
+which would give the level, is missing)."""
+import numpy as np
+import pytest
+
+import lbm_inputs as li
+from oracle import oracle as ora
+from oracle import riemann
+from tests.parity import assert_parity, conditioned_tolerance, run_gpu, run_oracle, sensitivity
+
+pytestmark = pytest.mark.gpu
+
+LEFT, RIGHT = (4.0, 0.0, 1.0), (1.0, 0.0, 1.0)
+
+
+def l1_vs_exact(gpu, nx, gamma, steps, r):
+    er, eu, eT = riemann.shock_tube_profile((4.0, 0.0, 4.0), (1.0, 0.0, 1.0), gamma, nx,
+                                            riemann.lattice_time(steps, nx, r))
+    return [riemann.l1_error(gpu[0][:nx], er), riemann.l1_error(gpu[1][0][:nx], eu),
+            riemann.l1_error(gpu[2][:nx], eT)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_paper_tube_3d_1000x16x16(prec):
+    lat, nx, steps, gamma, tau = ora.D3Q107, 1000, 180, 1.4, 2.0 / 3.0
+    bc = (ora.ZERO_GRADIENT, ora.PERIODIC, ora.PERIODIC)
+    f1 = li.sod_fields(nx, 1, 1, D=3, left=LEFT, right=RIGHT)
+    ref, _ = run_oracle(lat, gamma, tau, tau, (nx, 1, 1), bc, f1, steps)
+    kappa = sensitivity(lat, gamma, tau, tau, (nx, 1, 1), bc, f1, steps, prec, ref=ref)
+    gpu, _ = run_gpu(1, gamma, tau, tau, (nx, 16, 16), bc, li.sod_fields(nx, 16, 16, D=3, left=LEFT, right=RIGHT),
+                     steps, prec)
+    # uniform across the tube: every (y, z) row equals row 0 bitwise
+    for q in (gpu[0], gpu[2], gpu[1][0]):
+        rows = q.reshape(16 * 16, nx)
+        assert np.all(rows == rows[0])
+    g0 = (gpu[0][:nx], gpu[1][:, :nx], gpu[2][:nx])
+    assert_parity(g0, ref, gamma, conditioned_tolerance(prec, kappa, steps))
+    _, _, r = ora.lattice_info(lat)
+    e = l1_vs_exact(gpu, nx, gamma, steps, r)
+    assert e[0] < 0.03 and e[1] < 0.01 and e[2] < 0.01, e
+
+
+@pytest.mark.parametrize("gamma", [1.1, 1.3, 5.0 / 3.0, 2.0])
+def test_paper_tube_2d_gamma_sweep(gamma):
+    lat, nx, steps, tau = ora.D2Q37, 1000, 180, 2.0 / 3.0
+    bc = (ora.ZERO_GRADIENT, ora.PERIODIC)
+    f1 = li.sod_fields(nx, 1, left=LEFT, right=RIGHT)
+    ref, _ = run_oracle(lat, gamma, tau, tau, (nx, 1), bc, f1, steps)
+    kappa = sensitivity(lat, gamma, tau, tau, (nx, 1), bc, f1, steps, 0, ref=ref)
+    gpu, _ = run_gpu(0, gamma, tau, tau, (nx, 16), bc, li.sod_fields(nx, 16, left=LEFT, right=RIGHT), steps, 0)
+    g0 = (gpu[0][:nx], gpu[1][:, :nx], gpu[2][:nx])
+    assert_parity(g0, ref, gamma, conditioned_tolerance(0, kappa, steps))
+    _, _, r = ora.lattice_info(lat)
+    e = l1_vs_exact(gpu, nx, gamma, steps, r)
+    assert e[0] < 0.03 and e[1] < 0.02 and e[2] < 0.02, (gamma, e)
