@@ -454,6 +454,79 @@ void ora_step(ora_state* s, long nsteps) {
   for (long k = 0; k < nsteps; ++k) step_once(s);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Finite-difference variant of Sec. III: Eq. (16)/(17) with the convection */
+/* term discretised by the third-order upwind scheme along each axis.       */
+/* ------------------------------------------------------------------------ */
+
+/* Third-order upwind approximation of dq/dx at p along one axis, for a
+ * velocity component of sign `sgn` (Sec. III; the printed g_j is read as
+ * g_i):
+ *   sgn > 0:  [q(p-2) - 6 q(p-1) + 3 q(p) + 2 q(p+1)] / 6
+ *   sgn < 0:  [-q(p+2) + 6 q(p+1) - 3 q(p) - 2 q(p-1)] / 6
+ * Neighbours outside the grid follow the axis' boundary rule (periodic wrap
+ * or the edge cell).  `at(k)` reads q at axis position k. */
+static double upwind3(int p, int sgn, int n, int bc, const double* plane, long stride, long base) {
+#define Q_AT(k) plane[base + (long)pull_index((p), -(k), (n), (bc)) * stride]
+  double d;
+  if (sgn > 0)
+    d = (Q_AT(-2) - 6.0 * Q_AT(-1) + 3.0 * Q_AT(0) + 2.0 * Q_AT(1)) / 6.0;
+  else
+    d = (-Q_AT(2) + 6.0 * Q_AT(1) - 3.0 * Q_AT(0) - 2.0 * Q_AT(-1)) / 6.0;
+#undef Q_AT
+  return d;
+}
+
+/* One forward-Euler step of Eq. (16)/(17) with lambda = dt/dx:
+ *   g_i <- g_i - lambda sum_a xi_ia D_a(g_i) - (1/tau_f)(g_i - F_i)
+ *   h_i <- h_i - lambda sum_a xi_ia D_a(h_i) - (1/tau_g)(h_i - (delta/2) T F_i)
+ * with D_a the third-order upwind difference along axis a for the sign of
+ * xi_ia, and F, T from the cell's own moments at the old time level. */
+static void step_fd_once(ora_state* s, double lambda) {
+  const long N = s->N;
+  const int Q = s->L.Q, D = s->L.D;
+  const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
+  const long stride[3] = {1, nx, (long)nx * ny};
+  const double wf = 1.0 / s->tau_f, wg = 1.0 / s->tau_g;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y) {
+      double gc[107], hc[107], F[107], u[3], rho, T;
+      for (int x = 0; x < nx; ++x) {
+        const long cell = x + (long)nx * (y + (long)ny * z);
+        const int pos[3] = {x, y, z};
+        const int nn[3] = {nx, ny, nz};
+        for (int i = 0; i < Q; ++i) {
+          gc[i] = s->g[i * N + cell];
+          hc[i] = s->h[i * N + cell];
+        }
+        cell_moments(&s->L, s->delta, gc, hc, &rho, u, &T);
+        equilibrium(&s->L, rho, u, T, F);
+        for (int i = 0; i < Q; ++i) {
+          double cg = 0.0, ch = 0.0;
+          for (int a = 0; a < D; ++a) {
+            const int c = s->L.c[i][a];
+            if (c == 0) continue;
+            const double xi = s->L.r * c;
+            const long base = cell - (long)pos[a] * stride[a];
+            cg += xi * upwind3(pos[a], c, nn[a], s->bc[a], s->g + i * N, stride[a], base);
+            ch += xi * upwind3(pos[a], c, nn[a], s->bc[a], s->h + i * N, stride[a], base);
+          }
+          const double Fh = 0.5 * s->delta * T * F[i];
+          s->g2[i * N + cell] = gc[i] - lambda * cg - wf * (gc[i] - F[i]);
+          s->h2[i * N + cell] = hc[i] - lambda * ch - wg * (hc[i] - Fh);
+        }
+      }
+    }
+  double* t;
+  t = s->g; s->g = s->g2; s->g2 = t;
+  t = s->h; s->h = s->h2; s->h2 = t;
+}
+
+void ora_step_fd(ora_state* s, long nsteps, double lambda) {
+  for (long k = 0; k < nsteps; ++k) step_fd_once(s, lambda);
+}
+
 /* rho, u (component-major), T of the stored state, per cell. */
 void ora_moments(const ora_state* s, double* rho, double* u, double* T) {
   const long N = s->N;

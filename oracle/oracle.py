@@ -56,6 +56,7 @@ def _load():
     lib.ora_free.argtypes = [ctypes.c_void_p]
     lib.ora_init.argtypes = [ctypes.c_void_p, dp, dp, dp]
     lib.ora_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+    lib.ora_step_fd.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_double]
     lib.ora_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
     lib.ora_conserved.argtypes = [ctypes.c_void_p, dp]
     lib.ora_get_pops.argtypes = [ctypes.c_void_p, dp, dp]
@@ -164,6 +165,10 @@ class Oracle:
 
     def step(self, n: int = 1):
         self._lib.ora_step(self._h, int(n))
+
+    def step_fd(self, n=1, lam=0.1):
+        """Finite-difference steps of Sec. III with lambda = dt/dx."""
+        self._lib.ora_step_fd(self._h, int(n), float(lam))
 
     def moments(self):
         rho = np.zeros(self.N)
