@@ -62,6 +62,10 @@ WORKLOADS = {
                   fields="sod",
                   desc="D2Q37 FP64 Sod shock tube 1000x4 (rho 1|0.125, p 1|0.1, zero-gradient x, periodic y), "
                        "gamma 1.4, tau 0.6, 500 steps per solve"),
+    "fd2d": dict(lattice=0, prec="f32", shape=(4096, 4096), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=200,
+                 fields="fourier2d", scheme="fd", lam=0.03,
+                 desc="D2Q37 FP32 finite-difference variant (Sec. III, third-order upwind, lambda 0.03), periodic "
+                      "4096x4096, recipe fields, 200 steps per solve"),
     "periodic2d_small": dict(lattice=0, prec="f32", shape=(1024, 1024), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=20,
                              fields="fourier2d",
                              desc="D2Q37 FP32 periodic 1024x1024 (profiling case, 0.6 GB state > L2), 20 steps"),
@@ -280,7 +284,10 @@ def run_ours(args, wl):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-        solver.step(S)
+        if wl.get("scheme") == "fd":
+            solver.step_fd(S, wl["lam"])
+        else:
+            solver.step(S)
         if ev_pairs is not None:
             b.record(stream)
             ev_pairs.append((a, b))
@@ -295,7 +302,8 @@ def run_ours(args, wl):
     # only the idle buffer; the state is untouched)
     from paper_1608_06345_gb300 import autotune
     solver.init(d_rho, d_u, d_T)
-    tuned = autotune.tune(solver, reps=5, cache_path=None)
+    tuned = autotune.tune(solver, reps=5, cache_path=None) if wl.get("scheme") != "fd" else \
+        {"index": -1, "stage": 0, "block": 128 if wl["lattice"] == 0 else 64}
 
     for _ in range(max(args.warmup, 0)):
         bench_step()
@@ -334,7 +342,10 @@ def run_ours(args, wl):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         lbm.lbm_init(solver.h, h_rho, h_u, h_T)
-        lbm.lbm_step(solver.h, S)
+        if wl.get("scheme") == "fd":
+            lbm.lbm_step_fd(solver.h, S, wl["lam"])
+        else:
+            lbm.lbm_step(solver.h, S)
         lbm.lbm_moments(solver.h, r_rho, r_u, r_T)
     barrier()
     e2e_dt = time.perf_counter() - t0
@@ -353,7 +364,8 @@ def run_ours(args, wl):
     bytes_per_cell = 2 * Q * 2 * word
     peak, peak_kind = measured_peaks()
     achieved = N * bytes_per_cell / step_kernel_s / 1e9
-    key = f"k_step_{'d2q37' if wl['lattice'] == 0 else 'd3q107'}_{wl['prec']}_{'x'.join(map(str, shape))}"
+    kname = "k_step_fd" if wl.get("scheme") == "fd" else "k_step"
+    key = f"{kname}_{'d2q37' if wl['lattice'] == 0 else 'd3q107'}_{wl['prec']}_{'x'.join(map(str, shape))}"
     traffic = recorded_traffic(key)
 
     cpu = None

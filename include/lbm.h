@@ -112,6 +112,16 @@ int lbm_step(lbm_handle h, long n);
  * step separately (the plain one-launch-per-step path). */
 int lbm_set_graph_steps(lbm_handle h, int steps);
 
+/* Advance n >= 0 time steps of the finite-difference variant of Sec. III:
+ * forward Euler in time, the convection xi_i . grad q_i discretised along
+ * each axis by the third-order upwind difference (the paper's printed g_j is
+ * read as g_i), and the BGK relaxation of Eq. (16)/(17) from the cell's own
+ * moments; lambda = dt/dx (> 0), tau_f and tau_g in units of dt.  Boundaries
+ * as for lbm_step.  Forward Euler with this stencil is stable only for small
+ * lambda (about 0.07 at tau = 0.8 on rough fields; the largest velocity
+ * 3 r moves 3 r lambda cells per step).  Asynchronous; plain launches. */
+int lbm_step_fd(lbm_handle h, long n, double lambda);
+
 /* rho, u, T of the stored (post-collision) state, Eq. (14)/(15), into host
  * arrays of N, D*N, N doubles.  Synchronises; returns LBM_ENONFINITE if any
  * step since creation met a non-finite density or temperature. */

@@ -347,9 +347,12 @@ __device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args
 // For 16-bit storage the accessors return the stored d, e and the new values
 // are formed directly in the stored scale:
 //   d* = d + omega_f (dF / gref - d),  e* = (hA / hs) dF + (1 - omega_g) e + hb gref / hs
-template <int LAT, class S, class C, bool IDX32, class GetG, class GetH>
-__device__ __forceinline__ void collide_store(GetG&& getg, GetH&& geth, const Args<C>& a, S* __restrict__ dst,
-                                              long long ps, unsigned cell) {
+// FD: the finite-difference variant of Sec. III, which relaxes the cell's own
+// values and subtracts the convection term conv(I) = {c_g, c_h} (in the
+// stored scale) from the relaxed values.
+template <int LAT, class S, class C, bool IDX32, bool FD, class GetG, class GetH, class Conv>
+__device__ __forceinline__ void collide_store_impl(GetG&& getg, GetH&& geth, Conv&& conv, const Args<C>& a,
+                                                   S* __restrict__ dst, long long ps, unsigned cell) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
   constexpr bool SCALED = IsS16<S>::value;
@@ -380,17 +383,40 @@ __device__ __forceinline__ void collide_store(GetG&& getg, GetH&& geth, const Ar
         hAs = hA * a.inv_hscale[g];
         hbg = hbs * a.gref[g] * a.inv_hscale[g];
       }
-      const C dn = fma(a.omega_f, fma(dF, ig, -gi), gi);
-      const C en = fma(hAs, dF, fma(om1, hi, hbg));
+      C dn = fma(a.omega_f, fma(dF, ig, -gi), gi);
+      C en = fma(hAs, dF, fma(om1, hi, hbg));
+      if constexpr (FD) {
+        const auto cv = conv(I);
+        dn -= cv.g;
+        en -= cv.h;
+      }
       st(i, f_to_s16<S>(static_cast<float>(dn)));
       st(Q + i, f_to_s16<S>(static_cast<float>(en)));
     } else {
-      const C gn = fma(a.omega_f, dF - gi, gi);
-      const C hn = fma(hA, dF, fma(om1, hi, hbs * a.gref[g]));
+      C gn = fma(a.omega_f, dF - gi, gi);
+      C hn = fma(hA, dF, fma(om1, hi, hbs * a.gref[g]));
+      if constexpr (FD) {
+        const auto cv = conv(I);
+        gn -= cv.g;
+        hn -= cv.h;
+      }
       st(i, static_cast<S>(gn));
       st(Q + i, static_cast<S>(hn));
     }
   });
+}
+
+template <class C>
+struct ConvGH {
+  C g, h;
+};
+
+// the stream-and-collide form: no convection term
+template <int LAT, class S, class C, bool IDX32, class GetG, class GetH>
+__device__ __forceinline__ void collide_store(GetG&& getg, GetH&& geth, const Args<C>& a, S* __restrict__ dst,
+                                              long long ps, unsigned cell) {
+  collide_store_impl<LAT, S, C, IDX32, false>(getg, geth, [](auto) { return ConvGH<C>{C(0), C(0)}; }, a, dst, ps,
+                                              cell);
 }
 
 // raw value of a stored population in the compute type (16-bit: the stored
@@ -504,6 +530,77 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
 template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false>
 __global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
   step_cell<LAT, S, C, STAGE, BX, IDX32>(src, dst, a, blockIdx.x * BX + threadIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// the finite-difference variant of Sec. III (Eq. (16)/(17) with the
+// convection term discretised along each axis by the third-order upwind
+// difference; the printed g_j is read as g_i), lamr = lambda r, lambda = dt/dx:
+//   q*_i = q_i - lambda xi_i . D(q_i) - omega (q_i - Q_eq,i)
+//   D_a(q) at p for c_a > 0: [q(p-2) - 6 q(p-1) + 3 q(p) + 2 q(p+1)] / 6
+//                 for c_a < 0: [-q(p+2) + 6 q(p+1) - 3 q(p) - 2 q(p-1)] / 6
+// One thread per cell; the own 2Q values in registers, the upwind neighbours
+// read per direction (their reuse across the block is served by L1/L2).
+// ---------------------------------------------------------------------------
+template <int LAT, class S, class C, int BX>
+__global__ void __launch_bounds__(BX) k_step_fd(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a,
+                                                C lamr) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const int x = blockIdx.x * BX + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  if (x >= nx) return;
+  // positions p + k, k = -2..2 (index k + 2), after the boundary rule
+  unsigned xp[5], yp[5], zp[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    xp[k] = (unsigned)pull_coord(x, 2 - k, nx, a.bc[0]);
+    yp[k] = (unsigned)pull_coord(y, 2 - k, ny, a.bc[1]) * (unsigned)nx;
+    zp[k] = (L::D == 3) ? (unsigned)pull_coord(z, 2 - k, nz, a.bc[2]) * (unsigned)nx * (unsigned)ny : 0u;
+  }
+  const unsigned cell = xp[2] + yp[2] + zp[2];
+  const long long ps = a.ps;
+  auto q = [&](int plane, unsigned idx) -> C { return raw_value<S, C>(ldg_s(src + plane * ps + idx)); };
+  C g[Q], h[Q];
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    g[i] = q(i, cell);
+    h[i] = q(Q + i, cell);
+  });
+  // upwind difference of plane `pl` along one axis with stride table `pos`
+  // (the other two axes at the cell's own position `rest`)
+  auto upwind = [&](int pl, int sgn, const unsigned (&pos)[5], unsigned rest, C own) -> C {
+    if (sgn > 0)
+      return (q(pl, pos[0] + rest) - C(6) * q(pl, pos[1] + rest) + C(3) * own + C(2) * q(pl, pos[3] + rest)) *
+             C(1.0 / 6.0);
+    return (-q(pl, pos[4] + rest) + C(6) * q(pl, pos[3] + rest) - C(3) * own - C(2) * q(pl, pos[1] + rest)) *
+           C(1.0 / 6.0);
+  };
+  auto conv = [&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+    C cg = C(0), ch = C(0);
+    if constexpr (cx != 0) {
+      const unsigned rest = yp[2] + zp[2];
+      cg = fma(C(cx), upwind(i, cx, xp, rest, g[i]), cg);
+      ch = fma(C(cx), upwind(Q + i, cx, xp, rest, h[i]), ch);
+    }
+    if constexpr (cy != 0) {
+      const unsigned rest = xp[2] + zp[2];
+      cg = fma(C(cy), upwind(i, cy, yp, rest, g[i]), cg);
+      ch = fma(C(cy), upwind(Q + i, cy, yp, rest, h[i]), ch);
+    }
+    if constexpr (cz != 0) {
+      const unsigned rest = xp[2] + yp[2];
+      cg = fma(C(cz), upwind(i, cz, zp, rest, g[i]), cg);
+      ch = fma(C(cz), upwind(Q + i, cz, zp, rest, h[i]), ch);
+    }
+    return ConvGH<C>{lamr * cg, lamr * ch};
+  };
+  collide_store_impl<LAT, S, C, false, true>([&](auto I) { return g[decltype(I)::value]; },
+                                             [&](auto I) { return h[decltype(I)::value]; }, conv, a, dst, ps,
+                                             cell);
 }
 
 // ---------------------------------------------------------------------------

@@ -139,6 +139,17 @@ cudaError_t launch_step_plain(const Instance* inst, const void* src, void* dst) 
   return launch_step_shape<LAT, S, C>(inst, src, dst, false);
 }
 
+// the finite-difference step (lam = dt/dx): 128 cells per block in 2D, 64 in 3D
+template <int LAT, class S, class C>
+cudaError_t launch_step_fd_t(const Instance* inst, const void* src, void* dst, double lam) {
+  constexpr int BX = (LAT == 0) ? 128 : 64;
+  const dim3 grid((unsigned)((inst->n[0] + BX - 1) / BX), (unsigned)inst->n[1], (unsigned)inst->n[2]);
+  const Args<C>& a = args_of<C>(inst);
+  k_step_fd<LAT, S, C, BX><<<grid, BX, 0, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst), a,
+                                                          static_cast<C>(lam * inst->table.r));
+  return cudaGetLastError();
+}
+
 // pool: the shape of the batched step per (lattice, storage)
 template <int LAT, class S>
 struct PoolShape {

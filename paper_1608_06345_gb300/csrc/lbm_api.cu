@@ -407,6 +407,20 @@ int lbm_step(lbm_handle h, long n) {
   return LBM_OK;
 }
 
+int lbm_step_fd(lbm_handle h, long n, double lambda) {
+  if (!h) return fail(LBM_EINVAL, "handle is NULL");
+  if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(LBM_EINVAL, "lambda = dt/dx must be > 0");
+  if (h->N == 0) return LBM_OK;
+  for (long k = 0; k < n; ++k) {
+    cudaError_t e = launchers_of(h).step_fd(h, h->buf[h->cur], h->buf[1 - h->cur], lambda);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the finite-difference step");
+    h->cur ^= 1;
+    ++h->steps_done;
+  }
+  return LBM_OK;
+}
+
 int lbm_moments_device(lbm_handle h, double* rho, double* u, double* T) {
   if (!h) return fail(LBM_EINVAL, "handle is NULL");
   if (h->N > 0 && (!rho || !u || !T)) return fail(LBM_EINVAL, "field pointer is NULL");

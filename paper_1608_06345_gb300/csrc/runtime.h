@@ -81,6 +81,7 @@ struct Launchers {
   int (*shape_count)();
   void (*shape_get)(int k, int* stage, int* bx);
   cudaError_t (*configure)(const Instance* inst);
+  cudaError_t (*step_fd)(const Instance* inst, const void* src, void* dst, double lam);
 };
 
 extern const Launchers kLaunchers_0_0, kLaunchers_0_1, kLaunchers_0_2, kLaunchers_0_3;

@@ -42,6 +42,7 @@ extern const Launchers LBM_CAT(kLaunchers, LBM_LAT, LBM_PREC) = {
     &shape_count_t<LBM_LAT, StoreT>,
     &shape_get_t<LBM_LAT, StoreT>,
     &configure_step_t<LBM_LAT, StoreT, ComputeT>,
+    &launch_step_fd_t<LBM_LAT, StoreT, ComputeT>,
 };
 
 }  // namespace lbm

@@ -34,7 +34,7 @@ EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init
            "lbm_conserved_noalloc", "lbm_pool_bytes", "lbm_pool_create", "lbm_pool_destroy",
            "lbm_pool_instance_bytes", "lbm_pool_submit", "lbm_pool_run", "lbm_pool_sync", "lbm_pool_poll",
            "lbm_pool_result", "lbm_pool_stats", "lbm_shape_info", "lbm_set_shape", "lbm_get_shape",
-           "lbm_autotune", "lbm_set_graph_steps", "lbm_quadrature"]
+           "lbm_autotune", "lbm_set_graph_steps", "lbm_quadrature", "lbm_step_fd"]
 
 
 class LbmError(RuntimeError):
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = False):
         "lbm_init": (ctypes.c_int, [vp, vp, vp, vp]),
         "lbm_init_device": (ctypes.c_int, [vp, vp, vp, vp]),
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_long]),
+        "lbm_step_fd": (ctypes.c_int, [vp, ctypes.c_long, ctypes.c_double]),
         "lbm_moments": (ctypes.c_int, [vp, vp, vp, vp]),
         "lbm_moments_device": (ctypes.c_int, [vp, vp, vp, vp]),
         "lbm_conserved": (ctypes.c_int, [vp, dp]),
@@ -184,6 +185,10 @@ def lbm_init_device(h, rho, u, T):
 
 def lbm_step(h, n):
     return _check(load().lbm_step(h, int(n)))
+
+
+def lbm_step_fd(h, n, lam):
+    return _check(load().lbm_step_fd(h, int(n), float(lam)))
 
 
 def lbm_moments(h, rho, u, T):
@@ -345,6 +350,10 @@ class Solver:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def step_fd(self, n=1, lam=0.05):
+        """Finite-difference steps (Sec. III) with lambda = dt/dx."""
+        lbm_step_fd(self.h, n, lam)
 
     def moments(self):
         rho = np.zeros(self.N)
