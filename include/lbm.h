@@ -144,13 +144,14 @@ long lbm_steps_done(lbm_handle h);
 
 /* Copy the raw population planes of the current state to or from host
  * memory of lbm_raw_state_bytes() bytes, for checkpoint/restore.
- * Synchronous.  Layout: 2Q planes of N values in the storage type (g for
- * velocities 0..Q-1, then h), velocity order of lbm_lattice_table.  Values
- * are deviations from the instance's reference equilibrium gref_i =
- * F_i(rho0, u = 0, T0), href_i = (delta/2) T0 gref_i: g_i - gref_i and
- * h_i - href_i for FP64/FP32 storage; (g_i - gref_i)/gref_i and
- * (h_i - href_i)/hscale_i (hscale_i = href_i, or gref_i when delta = 0) for
- * 16-bit storage. */
+ * Synchronous.  Velocity order of lbm_lattice_table.  Layout:
+ *  - FP64/FP32 storage: 2Q planes of N values (g for velocities 0..Q-1,
+ *    then h), the values g_i - gref_i and h_i - href_i;
+ *  - 16-bit storage: Q planes of N 4-byte pairs (g_i in the low 16 bits, h_i
+ *    in the high 16 bits), the values (g_i - gref_i)/gref_i and
+ *    (h_i - href_i)/hscale_i.
+ * gref_i = F_i(rho0, u = 0, T0) is the instance's reference equilibrium,
+ * href_i = (delta/2) T0 gref_i, hscale_i = href_i (gref_i when delta = 0). */
 size_t lbm_raw_state_bytes(lbm_handle h);
 int lbm_get_state(lbm_handle h, void* host, size_t bytes);
 int lbm_set_state(lbm_handle h, const void* host, size_t bytes);
@@ -167,9 +168,10 @@ int lbm_lattice_table(int lattice, int* q, int* c, double* w, double* r);
  * call cudaMalloc when they need the totals -- e.g. a serving pool that has
  * reserved the whole device budget, or code holding populations in its own
  * arena without a library instance.
- *  state         device pointer to 2Q planes in the layout of lbm_get_state
- *                (deviations from the reference equilibrium of rho0, T0),
- *                plane p at element offset p * plane_stride
+ *  state         device pointer to the planes in the layout of lbm_get_state
+ *                (deviations from the reference equilibrium of rho0, T0);
+ *                plane p starts plane_stride elements (pairs, for 16-bit
+ *                storage) after plane p - 1
  *  ncells        cells per plane, 0 <= ncells <= 16777216 (4096^2 or 256^3);
  *                larger sizes fail with LBM_EINVAL
  *  lattice, prec, gamma, rho0, T0: as given to lbm_create (rho0, T0 <= 0

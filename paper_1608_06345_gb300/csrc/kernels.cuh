@@ -142,6 +142,68 @@ __device__ __forceinline__ S encode(C v, int g, const Args<C>& a) {
 }
 
 // ---------------------------------------------------------------------------
+// population addressing
+//   FP64 / FP32 storage: plane p (0..Q-1 for g, Q..2Q-1 for h), element
+//     p * ps + cell;
+//   16-bit storage: g_i and h_i of a cell are adjacent, one 32-bit pair
+//     (g in the low half): plane i holds ps pairs, pair i * ps + cell.  One
+//     access moves both populations of a direction.
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ void unpack16(unsigned v, float& lo, float& hi) {
+  if constexpr (std::is_same<S, __half>::value) {
+    lo = __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+    hi = __half2float(__ushort_as_half((unsigned short)(v >> 16)));
+  } else {  // bfloat16: the upper 16 bits of an FP32
+    lo = __uint_as_float(v << 16);
+    hi = __uint_as_float(v & 0xffff0000u);
+  }
+}
+
+template <class S>
+__device__ __forceinline__ unsigned pack16(float lo, float hi) {
+  if constexpr (std::is_same<S, __half>::value)
+    return (unsigned)__half_as_ushort(__float2half_rn(lo)) | ((unsigned)__half_as_ushort(__float2half_rn(hi)) << 16);
+  else
+    return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+// raw stored (g_i, h_i) of a cell (16-bit: the stored relative deviations)
+template <int Q, class S, class C>
+__device__ __forceinline__ void ld_gh(const S* __restrict__ src, int i, long long ps, size_t cell, C& g, C& h) {
+  if constexpr (IsS16<S>::value) {
+    float lo, hi;
+    unpack16<S>(__ldg(reinterpret_cast<const unsigned*>(src) + ((size_t)i * ps + cell)), lo, hi);
+    g = static_cast<C>(lo);
+    h = static_cast<C>(hi);
+  } else {
+    g = static_cast<C>(__ldg(src + ((size_t)i * ps + cell)));
+    h = static_cast<C>(__ldg(src + ((size_t)(Q + i) * ps + cell)));
+  }
+}
+
+// store raw (g_i, h_i) (already in the stored scale)
+template <int Q, class S, class C>
+__device__ __forceinline__ void st_gh(S* __restrict__ dst, int i, long long ps, size_t cell, C g, C h) {
+  if constexpr (IsS16<S>::value) {
+    reinterpret_cast<unsigned*>(dst)[(size_t)i * ps + cell] = pack16<S>(static_cast<float>(g), static_cast<float>(h));
+  } else {
+    dst[(size_t)i * ps + cell] = static_cast<S>(g);
+    dst[(size_t)(Q + i) * ps + cell] = static_cast<S>(h);
+  }
+}
+
+// deviations (dg, dh) of a stored raw pair of group grp
+template <class S, class C>
+__device__ __forceinline__ void scale_gh(C& g, C& h, int grp, const Args<C>& a) {
+  if constexpr (IsS16<S>::value) {
+    g *= a.gref[grp];
+    h *= a.hscale[grp];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // equilibrium deviations (Eq. (18), regrouped by powers of s per group)
 //
 // With u2 = |u|^2, t = T - 1, x2 = |xi|^2 of the group:
@@ -390,8 +452,11 @@ __device__ __forceinline__ void collide_store_impl(GetG&& getg, GetH&& geth, Con
         dn -= cv.g;
         en -= cv.h;
       }
-      st(i, f_to_s16<S>(static_cast<float>(dn)));
-      st(Q + i, f_to_s16<S>(static_cast<float>(en)));
+      // one 32-bit (g_i, h_i) pair
+      unsigned* dp = reinterpret_cast<unsigned*>(dst);
+      const unsigned pv = pack16<S>(static_cast<float>(dn), static_cast<float>(en));
+      if constexpr (IDX32) dp[(unsigned)i * (unsigned)ps + cell] = pv;
+      else dp[(size_t)i * ps + cell] = pv;
     } else {
       C gn = fma(a.omega_f, dF - gi, gi);
       C hn = fma(hA, dF, fma(om1, hi, hbs * a.gref[g]));
@@ -469,7 +534,15 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     C g[Q], h[Q];
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      if constexpr (IDX32) {
+      if constexpr (IsS16<S>::value) {  // one 32-bit pair holds g_i and h_i
+        const unsigned* sp = reinterpret_cast<const unsigned*>(src);
+        const unsigned v = IDX32 ? __ldg(sp + ((unsigned)i * (unsigned)ps + src_off(I)))
+                                 : __ldg(sp + ((size_t)i * ps + src_off(I)));
+        float lo, hi;
+        unpack16<S>(v, lo, hi);
+        g[i] = lo;
+        h[i] = hi;
+      } else if constexpr (IDX32) {
         const unsigned off = src_off(I);
         g[i] = raw_value<S, C>(ldg_s(src + ((unsigned)i * (unsigned)ps + off)));
         h[i] = raw_value<S, C>(ldg_s(src + ((unsigned)(Q + i) * (unsigned)ps + off)));
@@ -514,6 +587,9 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
                      "n"(sizeof(S)));
         asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa1),
                      "l"(sb + (size_t)(Q + i) * pb + offb), "n"(sizeof(S)));
+      } else if constexpr (IsS16<S>::value) {  // the 32-bit (g_i, h_i) pair into slot [i][t]
+        reinterpret_cast<unsigned*>(smem_raw)[i * BX + t] =
+            __ldg(reinterpret_cast<const unsigned*>(src) + ((size_t)i * ps + src_off(I)));
       } else {
         sg[i * BX + t] = ld(I, i, offb);
         sg[(Q + i) * BX + t] = ld(I, Q + i, offb);
@@ -521,9 +597,25 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     });
     if constexpr (STAGE == 1) asm volatile("cp.async.wait_all;\n" ::: "memory");
     // each thread reads back only the slots it filled itself
-    collide_store<LAT, S, C, IDX32>(
-        [&](auto I) { return raw_value<S, C>(sg[decltype(I)::value * BX + t]); },
-        [&](auto I) { return raw_value<S, C>(sg[(Q + decltype(I)::value) * BX + t]); }, a, dst, ps, cell);
+    if constexpr (IsS16<S>::value) {
+      const unsigned* sp = reinterpret_cast<const unsigned*>(smem_raw);
+      collide_store<LAT, S, C, IDX32>(
+          [&](auto I) {
+            float lo, hi;
+            unpack16<S>(sp[decltype(I)::value * BX + t], lo, hi);
+            return static_cast<C>(lo);
+          },
+          [&](auto I) {
+            float lo, hi;
+            unpack16<S>(sp[decltype(I)::value * BX + t], lo, hi);
+            return static_cast<C>(hi);
+          },
+          a, dst, ps, cell);
+    } else {
+      collide_store<LAT, S, C, IDX32>(
+          [&](auto I) { return raw_value<S, C>(sg[decltype(I)::value * BX + t]); },
+          [&](auto I) { return raw_value<S, C>(sg[(Q + decltype(I)::value) * BX + t]); }, a, dst, ps, cell);
+    }
   }
 }
 
@@ -561,40 +653,41 @@ __global__ void __launch_bounds__(BX) k_step_fd(const S* __restrict__ src, S* __
   }
   const unsigned cell = xp[2] + yp[2] + zp[2];
   const long long ps = a.ps;
-  auto q = [&](int plane, unsigned idx) -> C { return raw_value<S, C>(ldg_s(src + plane * ps + idx)); };
   C g[Q], h[Q];
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    g[i] = q(i, cell);
-    h[i] = q(Q + i, cell);
+    ld_gh<Q, S, C>(src, i, ps, cell, g[i], h[i]);
   });
-  // upwind difference of plane `pl` along one axis with stride table `pos`
-  // (the other two axes at the cell's own position `rest`)
-  auto upwind = [&](int pl, int sgn, const unsigned (&pos)[5], unsigned rest, C own) -> C {
-    if (sgn > 0)
-      return (q(pl, pos[0] + rest) - C(6) * q(pl, pos[1] + rest) + C(3) * own + C(2) * q(pl, pos[3] + rest)) *
-             C(1.0 / 6.0);
-    return (-q(pl, pos[4] + rest) + C(6) * q(pl, pos[3] + rest) - C(3) * own - C(2) * q(pl, pos[1] + rest)) *
-           C(1.0 / 6.0);
+  // upwind differences of g_i and h_i along one axis with position table
+  // `pos` (the other two axes at the cell's own position `rest`)
+  auto upwind = [&](int i, int sgn, const unsigned (&pos)[5], unsigned rest, C og, C oh, C& dg, C& dh) {
+    C gm2, hm2, gm1, hm1, gp1, hp1;  // values at the upwind-2, upwind-1 and downwind-1 positions
+    const int u2 = sgn > 0 ? 0 : 4, u1 = sgn > 0 ? 1 : 3, d1 = sgn > 0 ? 3 : 1;
+    ld_gh<Q, S, C>(src, i, ps, pos[u2] + rest, gm2, hm2);
+    ld_gh<Q, S, C>(src, i, ps, pos[u1] + rest, gm1, hm1);
+    ld_gh<Q, S, C>(src, i, ps, pos[d1] + rest, gp1, hp1);
+    const C sg = sgn > 0 ? C(1) : C(-1);
+    dg = sg * (gm2 - C(6) * gm1 + C(3) * og + C(2) * gp1) * C(1.0 / 6.0);
+    dh = sg * (hm2 - C(6) * hm1 + C(3) * oh + C(2) * hp1) * C(1.0 / 6.0);
   };
   auto conv = [&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-    C cg = C(0), ch = C(0);
+    C cg = C(0), ch = C(0), dg, dh;
     if constexpr (cx != 0) {
-      const unsigned rest = yp[2] + zp[2];
-      cg = fma(C(cx), upwind(i, cx, xp, rest, g[i]), cg);
-      ch = fma(C(cx), upwind(Q + i, cx, xp, rest, h[i]), ch);
+      upwind(i, cx, xp, yp[2] + zp[2], g[i], h[i], dg, dh);
+      cg = fma(C(cx), dg, cg);
+      ch = fma(C(cx), dh, ch);
     }
     if constexpr (cy != 0) {
-      const unsigned rest = xp[2] + zp[2];
-      cg = fma(C(cy), upwind(i, cy, yp, rest, g[i]), cg);
-      ch = fma(C(cy), upwind(Q + i, cy, yp, rest, h[i]), ch);
+      upwind(i, cy, yp, xp[2] + zp[2], g[i], h[i], dg, dh);
+      cg = fma(C(cy), dg, cg);
+      ch = fma(C(cy), dh, ch);
     }
     if constexpr (cz != 0) {
-      const unsigned rest = xp[2] + yp[2];
-      cg = fma(C(cz), upwind(i, cz, zp, rest, g[i]), cg);
-      ch = fma(C(cz), upwind(Q + i, cz, zp, rest, h[i]), ch);
+      upwind(i, cz, zp, xp[2] + yp[2], g[i], h[i], dg, dh);
+      cg = fma(C(cz), dg, cg);
+      ch = fma(C(cz), dh, ch);
     }
     return ConvGH<C>{lamr * cg, lamr * ch};
   };
@@ -670,8 +763,10 @@ __global__ void k_init(S* __restrict__ dst, const double* __restrict__ rho, cons
   const long long ps = a.ps;
   equilibrium_dev<LAT, C>(drho, uu, dT, a, [&](auto I, C dF, C dFh) {
     constexpr int i = decltype(I)::value;
-    dst[i * ps + cell] = encode<S, C, false>(dF, L::grp(i), a);
-    dst[(Q + i) * ps + cell] = encode<S, C, true>(dFh, L::grp(i), a);
+    if constexpr (IsS16<S>::value)
+      st_gh<Q, S, C>(dst, i, ps, cell, dF * a.inv_gref[L::grp(i)], dFh * a.inv_hscale[L::grp(i)]);
+    else
+      st_gh<Q, S, C>(dst, i, ps, cell, dF, dFh);
   });
 }
 
@@ -687,17 +782,14 @@ __global__ void k_moments(const S* __restrict__ src, double* __restrict__ rho, d
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= N) return;
   const long long ps = a.ps;
+  C g[Q], h[Q];
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    ld_gh<Q, S, C>(src, i, ps, cell, g[i], h[i]);
+  });
   C drho, uu[3], dT;
-  moments_dev<LAT, C>(
-      [&](auto I) {
-        constexpr int i = decltype(I)::value;
-        return decode<S, C, false>(src[i * ps + cell], L::grp(i), a);
-      },
-      [&](auto I) {
-        constexpr int i = decltype(I)::value;
-        return decode<S, C, true>(src[(Q + i) * ps + cell], L::grp(i), a);
-      },
-      a, drho, uu, dT);
+  moments_raw<LAT, C, IsS16<S>::value>([&](auto I) { return g[decltype(I)::value]; },
+                                       [&](auto I) { return h[decltype(I)::value]; }, a, drho, uu, dT);
   rho[cell] = rho0 + static_cast<double>(drho);
   u[cell] = static_cast<double>(uu[0]);
   u[N + cell] = static_cast<double>(uu[1]);
@@ -705,12 +797,19 @@ __global__ void k_moments(const S* __restrict__ src, double* __restrict__ rho, d
   T[cell] = T0 + static_cast<double>(dT);
 }
 
-// decode a stored value to double for the FP64 reductions (16-bit codec in
-// FP32, as the step evaluates it)
-template <class S, bool IS_H>
-__device__ __forceinline__ double decode_d(S v, int g, const Args<float>& af) {
-  if constexpr (IsS16<S>::value) return static_cast<double>(decode<S, float, IS_H>(v, g, af));
-  else return static_cast<double>(v);
+// deviations (dg_i, dh_i) of a cell in double for the FP64 reductions
+// (16-bit codec evaluated in FP32, as the step evaluates it)
+template <int Q, class S>
+__device__ __forceinline__ void decode_pair_d(const S* __restrict__ src, int i, long long ps, size_t cell, int grp,
+                                              const Args<float>& af, double& g, double& h) {
+  if constexpr (IsS16<S>::value) {
+    float gr, hr;
+    ld_gh<Q, S, float>(src, i, ps, cell, gr, hr);
+    g = static_cast<double>(gr * af.gref[grp]);
+    h = static_cast<double>(hr * af.hscale[grp]);
+  } else {
+    ld_gh<Q, S, double>(src, i, ps, cell, g, h);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -740,8 +839,8 @@ __global__ void __launch_bounds__(kRedThreads) k_conserve_partial(const S* __res
        cell += (long long)gridDim.x * blockDim.x) {
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const double gi = decode_d<S, false>(src[i * ps + cell], L::grp(i), af);
-      const double hi = decode_d<S, true>(src[(Q + i) * ps + cell], L::grp(i), af);
+      double gi, hi;
+      decode_pair_d<Q, S>(src, i, ps, cell, L::grp(i), af, gi, hi);
       acc[0] += gi;
       if constexpr (L::cx(i) != 0) acc[1] += (a.r * L::cx(i)) * gi;
       if constexpr (L::cy(i) != 0) acc[2] += (a.r * L::cy(i)) * gi;

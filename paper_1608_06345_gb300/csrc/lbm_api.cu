@@ -485,11 +485,15 @@ size_t lbm_raw_state_bytes(lbm_handle h) {
 int lbm_get_state(lbm_handle h, void* host, size_t bytes) {
   if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
   if (bytes < lbm_raw_state_bytes(h)) return fail(LBM_EINVAL, "host buffer too small");
-  const size_t plane = (size_t)h->N * h->word;
+  // 16-bit storage keeps (g_i, h_i) as one 4-byte pair: Q planes of pairs
+  const bool paired = (h->prec == kF32S16F || h->prec == kF32S16BF);
+  const size_t elem = paired ? 2 * h->word : h->word;
+  const int planes = paired ? h->Q : 2 * h->Q;
+  const size_t plane = (size_t)h->N * elem;
   unsigned char* dst = static_cast<unsigned char*>(host);
   const unsigned char* src = static_cast<const unsigned char*>(h->buf[h->cur]);
-  cudaError_t e = cudaMemcpy2DAsync(dst, plane, src, (size_t)h->ps * h->word, plane, 2 * h->Q,
-                                    cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = cudaMemcpy2DAsync(dst, plane, src, (size_t)h->ps * elem, plane, planes, cudaMemcpyDeviceToHost,
+                                    h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copying the state to the host");
   return LBM_OK;
@@ -498,10 +502,13 @@ int lbm_get_state(lbm_handle h, void* host, size_t bytes) {
 int lbm_set_state(lbm_handle h, const void* host, size_t bytes) {
   if (!h || !host) return fail(LBM_EINVAL, "NULL argument");
   if (bytes < lbm_raw_state_bytes(h)) return fail(LBM_EINVAL, "host buffer too small");
-  const size_t plane = (size_t)h->N * h->word;
+  const bool paired = (h->prec == kF32S16F || h->prec == kF32S16BF);
+  const size_t elem = paired ? 2 * h->word : h->word;
+  const int planes = paired ? h->Q : 2 * h->Q;
+  const size_t plane = (size_t)h->N * elem;
   unsigned char* dst = static_cast<unsigned char*>(h->buf[h->cur]);
-  cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)h->ps * h->word, host, plane, plane, 2 * h->Q,
-                                    cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)h->ps * elem, host, plane, plane, planes, cudaMemcpyHostToDevice,
+                                    h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copying the state to the device");
   return LBM_OK;

@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(kNaThreads) k_conserve_chunk(const S* __restri
   for (long long cell = begin + threadIdx.x; cell < end; cell += kNaThreads) {
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const double gi = decode_d<S, false>(src[i * ps + cell], L::grp(i), af);
-      const double hi = decode_d<S, true>(src[(Q + i) * ps + cell], L::grp(i), af);
+      double gi, hi;
+      decode_pair_d<Q, S>(src, i, ps, cell, L::grp(i), af, gi, hi);
       acc[0] += gi;
       if constexpr (L::cx(i) != 0) acc[1] += (r * L::cx(i)) * gi;
       if constexpr (L::cy(i) != 0) acc[2] += (r * L::cy(i)) * gi;

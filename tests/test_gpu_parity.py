@@ -187,23 +187,50 @@ def test_nonfinite_input_is_reported():
     assert ei.value.code == lbm.LBM_ENONFINITE
 
 
-def test_checkpoint_roundtrip():
+@pytest.mark.parametrize("lat,shape,prec", [(0, (40, 6), F64), (0, (40, 6), 2), (1, (12, 5, 4), 3)])
+def test_checkpoint_roundtrip(lat, shape, prec):
     from paper_1608_06345_gb300 import lbm
-    shape = (40, 6)
     fields = fields_for(shape, seed=5)
-    a = lbm.Solver(0, 1.4, 0.6, 0.7, shape, prec=F64)
+    a = lbm.Solver(lat, 1.4, 0.6, 0.7, shape, prec=prec)
     a.init(*fields)
     a.step(7)
     raw = np.zeros(lbm.lbm_raw_state_bytes(a.h), dtype=np.uint8)
     lbm.lbm_get_state(a.h, raw)
     a.step(5)
     ra = a.moments()
-    b = lbm.Solver(0, 1.4, 0.6, 0.7, shape, prec=F64)
+    b = lbm.Solver(lat, 1.4, 0.6, 0.7, shape, prec=prec)
     lbm.lbm_set_state(b.h, raw)
     b.step(5)
     rb = b.moments()
     for qa, qb in zip(ra, rb):
         assert np.array_equal(qa, qb)
+
+
+@pytest.mark.parametrize("prec,dt", [(2, np.float16), (3, None)])
+def test_raw_16bit_state_is_paired(prec, dt):
+    """16-bit raw state: Q planes of N 4-byte pairs, g_i in the low half and
+    h_i in the high half, each scaled by the reference equilibrium.  The
+    density decoded on the host from the g halves equals the library's."""
+    from paper_1608_06345_gb300 import lbm
+    shape = (33, 5)
+    N = shape[0] * shape[1]
+    rho0, T0 = 0.9, 1.1
+    s = lbm.Solver(0, 1.4, 0.6, 0.6, shape, prec=prec, rho0=rho0, T0=T0)
+    s.init(*fields_for(shape, seed=8))
+    s.step(3)
+    raw = np.zeros(lbm.lbm_raw_state_bytes(s.h), dtype=np.uint8)
+    lbm.lbm_get_state(s.h, raw)
+    assert raw.size == 37 * N * 4
+    halves = raw.view(np.uint16).reshape(37, N, 2)
+    lo = halves[:, :, 0]
+    if dt is not None:
+        g = lo.view(dt).astype(np.float64)
+    else:  # bfloat16: the upper 16 bits of an IEEE single
+        g = (lo.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    gref = ora.feq(ora.D2Q37, rho0, [0.0, 0.0], T0)
+    rho_host = (gref[:, None] * (1.0 + g)).sum(axis=0)
+    rho, _, _ = s.moments()
+    np.testing.assert_allclose(rho_host, rho, rtol=1e-6, atol=0)
 
 
 @pytest.mark.parametrize("lat,shape,prec", [(0, (150, 6), F64), (1, (40, 5, 4), F32)])

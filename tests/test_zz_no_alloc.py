@@ -31,7 +31,8 @@ def device_state(solver):
     return torch.from_numpy(raw).cuda()
 
 
-@pytest.mark.parametrize("lat,shape,prec", [(0, (300, 7), 0), (1, (40, 6, 5), 0), (0, (257, 9), 1)])
+@pytest.mark.parametrize("lat,shape,prec", [(0, (300, 7), 0), (1, (40, 6, 5), 0), (0, (257, 9), 1),
+                                            (0, (300, 7), 2), (1, (20, 6, 5), 3)])
 def test_noalloc_totals_match_lbm_conserved_twice(lat, shape, prec):
     import torch
 
