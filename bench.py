@@ -38,10 +38,12 @@ L2_BYTES = 129 * 1024 * 1024
 # FP64 paths are bound by GB300's FP64 pipe, not by HBM.  Peak: 152 SMs x 2
 # FP64 instructions per clock x 2 flop (FMA) x 2.07 GHz = 1.259 TFLOP/s
 # (the GPU's nominal 1.25 TFLOP/s FP64 rate).  Flops per cell update of the
-# D2Q37 FP64 step from ncu's SASS counters (profiles/step_d2q37_f64.md):
-# 299 DFMA + 175 DADD + 95 DMUL per cell = 868 flop.
+# FP64 step from ncu's SASS counters of the plain one-thread-per-cell kernel
+# (profiles/step_d2q37_f64_1024.md, profiles/step_d3q107_f64_64.md):
+# D2Q37 299 DFMA + 175 DADD + 95 DMUL per cell = 868 flop;
+# D3Q107 786 DFMA + 511 DADD + 152 DMUL per cell = 2235 flop.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-FP64_FLOPS_PER_CELL = {0: 868}
+FP64_FLOPS_PER_CELL = {0: 868, 1: 2235}
 
 WORKLOADS = {
     # name: lattice, prec, shape, gamma, tau_f, tau_g, steps per solve, fields
@@ -82,6 +84,12 @@ WORKLOADS = {
                            steps=100, fields="fourier3d",
                            desc="D3Q107 FP32 periodic 256^3, same fields, gamma 1.3 (delta = 11/3), tau 0.6, "
                                 "100 steps per solve"),
+    "periodic3d_f64": dict(lattice=1, prec="f64", shape=(256, 256, 256), gamma=1.4, tau_f=0.6, tau_g=0.6,
+                           steps=10, fields="fourier3d",
+                           desc="D3Q107 FP64 periodic 256^3, same fields, gamma 1.4, tau 0.6, 10 steps per solve"),
+    "periodic3d_f64_small": dict(lattice=1, prec="f64", shape=(64, 64, 64), gamma=1.4, tau_f=0.6, tau_g=0.6,
+                                 steps=4, fields="fourier3d",
+                                 desc="D3Q107 FP64 periodic 64^3 (profiling case, 0.9 GB state > L2), 4 steps"),
     "periodic3d": dict(lattice=1, prec="f32", shape=(256, 256, 256), gamma=1.4, tau_f=0.6, tau_g=0.6, steps=100,
                        fields="fourier3d",
                        desc="D3Q107 FP32 periodic 256^3, 8-mode Fourier rho/u/T (seeds 3,4,5), gamma 1.4, "

@@ -250,11 +250,12 @@ __device__ __forceinline__ void eq_coeffs(C drho, const C (&u)[3], C dT, const A
   k.ur[2] = L::D == 3 ? a.r * u[2] : C(0);
 }
 
-// emit(I, dF_i) for every velocity i: the rest velocity, then the (c, -c)
-// pairs sharing the even part of the polynomial in s.  Velocities are
-// ordered by group, so a group's coefficients c0..c4 are formed once, at its
-// first pair, and are dead after its last.
-template <int LAT, class C, class Emit>
+// emit(I, dF_i) for every velocity i of [IB, IE): the rest velocity (when
+// IB = 0), then the (c, -c) pairs sharing the even part of the polynomial in
+// s.  Velocities are ordered by group, so a group's coefficients c0..c4 are
+// formed once, at its first pair in the range, and are dead after its last.
+// IB is 0 or odd, IE odd or Q (whole pairs only).
+template <int LAT, class C, int IB = 0, int IE = Lat<LAT>::Q, class Emit>
 __device__ __forceinline__ void eq_emit(const EqCoef<LAT, C>& k, const Args<C>& a, Emit&& emit) {
   using L = Lat<LAT>;
   C c0, c1, c2, c3, c4;
@@ -268,13 +269,16 @@ __device__ __forceinline__ void eq_emit(const EqCoef<LAT, C>& k, const Args<C>& 
     c3 = W * C(1.0 / 6.0);
     c4 = W * C(1.0 / 24.0);
   };
-  group(0);
-  emit(std::integral_constant<int, 0>{}, c0);
+  static_assert((IB == 0 || IB % 2 == 1) && (IE == L::Q || IE % 2 == 1) && IB < IE, "whole pairs only");
+  if constexpr (IB == 0) {
+    group(0);
+    emit(std::integral_constant<int, 0>{}, c0);
+  }
   static_for<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    if constexpr (i % 2 == 1) {
+    if constexpr (i % 2 == 1 && i >= IB && i < IE) {
       constexpr int g = L::grp(i);
-      if constexpr (L::grp(i - 1) != g) group(g);
+      if constexpr (i == IB || L::grp(i - 1) != g) group(g);
       constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
       C s = C(0);
       if constexpr (cx != 0) s = fma(C(cx), k.ur[0], s);
@@ -401,6 +405,86 @@ __device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args
   moments_raw<LAT, C, false>(getg, geth, a, drho, u, dT);
 }
 
+// The sums of moments_raw restricted to the velocities [IB, IE) (whole
+// pairs): acc = {sum dg, sum c_x dg, sum c_y dg, sum c_z dg,
+// r^2/2 sum c^2 dg + sum dh}.  Summing the parts of a partition gives the
+// cell's sums (up to rounding order).
+template <int LAT, class C, bool SCALED, int IB, int IE, class GetG, class GetH>
+__device__ __forceinline__ void moments_partial(GetG&& getg, GetH&& geth, const Args<C>& a, C (&acc)[5]) {
+  using L = Lat<LAT>;
+  C m = C(0), H = C(0);
+  if constexpr (IB == 0) {
+    if constexpr (SCALED) {
+      m = a.gref[0] * getg(std::integral_constant<int, 0>{});
+      H = a.hscale[0] * geth(std::integral_constant<int, 0>{});
+    } else {
+      m = getg(std::integral_constant<int, 0>{});
+      H = geth(std::integral_constant<int, 0>{});
+    }
+  }
+  C jx = C(0), jy = C(0), jz = C(0), k2 = C(0);
+  C s1 = C(1), s2 = C(2), s3 = C(3), sc2 = C(0), sh = C(1);
+  static_for<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (i % 2 == 1 && i >= IB && i < IE) {
+      constexpr int g = L::grp(i);
+      if constexpr (SCALED && (i == IB || L::grp(i - 1) != g)) {
+        s1 = a.gref[g];
+        s2 = C(2) * s1;
+        s3 = C(3) * s1;
+        sc2 = C(L::c2(i)) * s1;
+        sh = a.hscale[g];
+      }
+      auto mul = [&](int c) -> C {
+        const int ac = c < 0 ? -c : c;
+        const C v = ac == 1 ? s1 : (ac == 2 ? s2 : s3);
+        return c < 0 ? -v : v;
+      };
+      const C gp = getg(I), gm = getg(std::integral_constant<int, i + 1>{});
+      const C sp = gp + gm, df = gp - gm;
+      const C hp = geth(I) + geth(std::integral_constant<int, i + 1>{});
+      if constexpr (SCALED) {
+        m = fma(s1, sp, m);
+        if constexpr (L::cx(i) != 0) jx = fma(mul(L::cx(i)), df, jx);
+        if constexpr (L::cy(i) != 0) jy = fma(mul(L::cy(i)), df, jy);
+        if constexpr (L::cz(i) != 0) jz = fma(mul(L::cz(i)), df, jz);
+        k2 = fma(sc2, sp, k2);
+        H = fma(sh, hp, H);
+      } else {
+        m += sp;
+        if constexpr (L::cx(i) != 0) jx = fma(C(L::cx(i)), df, jx);
+        if constexpr (L::cy(i) != 0) jy = fma(C(L::cy(i)), df, jy);
+        if constexpr (L::cz(i) != 0) jz = fma(C(L::cz(i)), df, jz);
+        k2 = fma(C(L::c2(i)), sp, k2);
+        H += hp;
+      }
+    }
+  });
+  (void)s2;
+  (void)s3;
+  acc[0] = m;
+  acc[1] = jx;
+  acc[2] = jy;
+  acc[3] = jz;
+  acc[4] = fma(a.half_r2, k2, H);
+}
+
+// drho, u, dT of a cell from its summed partials (the closing lines of
+// moments_raw with dK + dH = acc[4])
+template <int LAT, class C>
+__device__ __forceinline__ void moments_finish(const C (&acc)[5], const Args<C>& a, C& drho, C (&u)[3], C& dT) {
+  using L = Lat<LAT>;
+  const C m = acc[0];
+  const C rho = a.rho0 + m;
+  const C inv = C(1) / rho;
+  drho = m;
+  u[0] = a.r * acc[1] * inv;
+  u[1] = a.r * acc[2] * inv;
+  u[2] = (L::D == 3) ? a.r * acc[3] * inv : C(0);
+  const C u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  dT = (C(2) * acc[4] - rho * u2 - a.Dd * a.T0 * m) * inv * a.inv_Dd;
+}
+
 // ---------------------------------------------------------------------------
 // collide one cell given its pulled deviations and store the result:
 //   g* = g~ + omega_f (dF - g~)
@@ -412,9 +496,14 @@ __device__ __forceinline__ void moments_dev(GetG&& getg, GetH&& geth, const Args
 // FD: the finite-difference variant of Sec. III, which relaxes the cell's own
 // values and subtracts the convection term conv(I) = {c_g, c_h} (in the
 // stored scale) from the relaxed values.
-template <int LAT, class S, class C, bool IDX32, bool FD, class GetG, class GetH, class Conv>
-__device__ __forceinline__ void collide_store_impl(GetG&& getg, GetH&& geth, Conv&& conv, const Args<C>& a,
-                                                   S* __restrict__ dst, long long ps, unsigned cell) {
+// relax_store: the relaxation and store of the velocities [IB, IE) of a cell
+// whose moments (drho, u, dT) are known; cell is the element index within a
+// plane (32 bits: below 2^32 cells per instance)
+template <int LAT, class S, class C, bool IDX32, bool FD, int IB = 0, int IE = Lat<LAT>::Q, class GetG, class GetH,
+          class Conv>
+__device__ __forceinline__ void relax_store(GetG&& getg, GetH&& geth, Conv&& conv, const Args<C>& a, C drho,
+                                            const C (&u)[3], C dT, S* __restrict__ dst, long long ps,
+                                            unsigned cell) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
   constexpr bool SCALED = IsS16<S>::value;
@@ -426,21 +515,18 @@ __device__ __forceinline__ void collide_store_impl(GetG&& getg, GetH&& geth, Con
     if constexpr (IDX32) dst[(unsigned)plane * (unsigned)ps + cell] = v;
     else *reinterpret_cast<S*>(db + (size_t)plane * pb) = v;
   };
-  C drho, u[3], dT;
-  moments_raw<LAT, C, SCALED>(getg, geth, a, drho, u, dT);
-  if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
   EqCoef<LAT, C> k;
   eq_coeffs<LAT, C>(drho, u, dT, a, k);
   const C hA = a.omega_g * a.half_delta * k.T;
   const C om1 = C(1) - a.omega_g;
   const C hbs = a.omega_g * a.half_delta * dT;
   C ig = C(1), hAs = hA, hbg = C(0);  // per-group: 1/gref, hA/hs, hbs gref/hs (16-bit)
-  eq_emit<LAT, C>(k, a, [&](auto I, C dF) {
+  eq_emit<LAT, C, IB, IE>(k, a, [&](auto I, C dF) {
     constexpr int i = decltype(I)::value;
     constexpr int g = L::grp(i);
     const C gi = getg(I), hi = geth(I);
     if constexpr (SCALED) {
-      if constexpr (i == 0 || L::grp(i == 0 ? 0 : i - 1) != g) {
+      if constexpr (i == IB || L::grp(i == 0 ? 0 : i - 1) != g) {
         ig = a.inv_gref[g];
         hAs = hA * a.inv_hscale[g];
         hbg = hbs * a.gref[g] * a.inv_hscale[g];
@@ -469,6 +555,15 @@ __device__ __forceinline__ void collide_store_impl(GetG&& getg, GetH&& geth, Con
       st(Q + i, static_cast<S>(hn));
     }
   });
+}
+
+template <int LAT, class S, class C, bool IDX32, bool FD, class GetG, class GetH, class Conv>
+__device__ __forceinline__ void collide_store_impl(GetG&& getg, GetH&& geth, Conv&& conv, const Args<C>& a,
+                                                   S* __restrict__ dst, long long ps, unsigned cell) {
+  C drho, u[3], dT;
+  moments_raw<LAT, C, IsS16<S>::value>(getg, geth, a, drho, u, dT);
+  if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+  relax_store<LAT, S, C, IDX32, FD>(getg, geth, conv, a, drho, u, dT, dst, ps, cell);
 }
 
 template <class C>
@@ -622,6 +717,104 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
 template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false>
 __global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
   step_cell<LAT, S, C, STAGE, BX, IDX32>(src, dst, a, blockIdx.x * BX + threadIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// the velocity-split step (STAGE 4): a block of P warps covers 32 cells of a
+// row; warp w pulls, sums and relaxes only its part [begin(w), end(w)) of the
+// velocities.  The parts' five partial sums meet in shared memory and every
+// warp adds them in the same order, so all parts use identical moments.
+// Each thread holds 2 (end - begin) values instead of 2Q, which keeps the
+// register count near that of the D2Q37 kernel for D3Q107.
+// ---------------------------------------------------------------------------
+template <int LAT, int P>
+struct Split {
+  static constexpr int NP = (Lat<LAT>::Q - 1) / 2;  // (c, -c) pairs
+  // part 0: the rest velocity and pairs [0, NP/P); part w: pairs [w NP/P, (w+1) NP/P)
+  __host__ __device__ static constexpr int begin(int w) { return w == 0 ? 0 : 1 + 2 * (w * NP / P); }
+  __host__ __device__ static constexpr int end(int w) { return 1 + 2 * ((w + 1) * NP / P); }
+  __host__ __device__ static constexpr int kmax() {
+    int m = 0;
+    for (int w = 0; w < P; ++w) m = (end(w) - begin(w) > m) ? end(w) - begin(w) : m;
+    return m;
+  }
+};
+
+template <int LAT, class S, class C, int P, int MINB>
+__global__ void __launch_bounds__(32 * P, MINB) k_step_split(const S* __restrict__ src, S* __restrict__ dst,
+                                                            const Args<C> a) {
+  using L = Lat<LAT>;
+  using SP = Split<LAT, P>;
+  constexpr int Q = L::Q;
+  constexpr int K = SP::kmax();
+  constexpr bool SCALED = IsS16<S>::value;
+  __shared__ C red[P][5][32];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int x = blockIdx.x * 32 + lane, y = blockIdx.y, z = blockIdx.z;
+  const bool active = x < nx;
+  const int xs = active ? x : nx - 1;  // lanes past the row end pull from a valid cell and store nothing
+  unsigned xo[7], yo[7], zo[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    xo[k] = (unsigned)pull_coord(xs, k - 3, nx, a.bc[0]);
+    yo[k] = (unsigned)pull_coord(y, k - 3, ny, a.bc[1]) * (unsigned)nx;
+    zo[k] = (L::D == 3) ? (unsigned)pull_coord(z, k - 3, nz, a.bc[2]) * (unsigned)nx * (unsigned)ny : 0u;
+  }
+  const unsigned cell = (unsigned)xs + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+  const long long ps = a.ps;
+  const char* sb = reinterpret_cast<const char*>(src);
+  const size_t pb = (size_t)ps * sizeof(S);
+  C g[K], h[K];
+  // phase 1: pull this warp's velocities and sum its partial moments
+  static_for<P>([&](auto W) {
+    constexpr int IB = SP::begin(decltype(W)::value), IE = SP::end(decltype(W)::value);
+    if (w == decltype(W)::value) {
+      static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (i >= IB && i < IE) {
+          const unsigned off = zo[L::cz(i) + 3] + yo[L::cy(i) + 3] + xo[L::cx(i) + 3];
+          if constexpr (SCALED) {
+            const unsigned v = __ldg(reinterpret_cast<const unsigned*>(src) + ((size_t)i * ps + off));
+            float lo, hi;
+            unpack16<S>(v, lo, hi);
+            g[i - IB] = lo;
+            h[i - IB] = hi;
+          } else {
+            const size_t offb = (size_t)off * sizeof(S);
+            g[i - IB] = static_cast<C>(ldg_s(reinterpret_cast<const S*>(sb + (size_t)i * pb + offb)));
+            h[i - IB] = static_cast<C>(ldg_s(reinterpret_cast<const S*>(sb + (size_t)(Q + i) * pb + offb)));
+          }
+        }
+      });
+      C acc[5];
+      moments_partial<LAT, C, SCALED, IB, IE>([&](auto I) { return g[decltype(I)::value - IB]; },
+                                              [&](auto I) { return h[decltype(I)::value - IB]; }, a, acc);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) red[w][k][lane] = acc[k];
+    }
+  });
+  __syncthreads();
+  C acc[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    C v = red[0][k][lane];
+#pragma unroll
+    for (int p = 1; p < P; ++p) v += red[p][k][lane];
+    acc[k] = v;
+  }
+  C drho, u[3], dT;
+  moments_finish<LAT, C>(acc, a, drho, u, dT);
+  if (!active) return;
+  if (w == 0 && !(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+  // phase 2: relax and store this warp's velocities
+  static_for<P>([&](auto W) {
+    constexpr int IB = SP::begin(decltype(W)::value), IE = SP::end(decltype(W)::value);
+    if (w == decltype(W)::value)
+      relax_store<LAT, S, C, false, false, IB, IE>(
+          [&](auto I) { return g[decltype(I)::value - IB]; }, [&](auto I) { return h[decltype(I)::value - IB]; },
+          [](auto) { return ConvGH<C>{C(0), C(0)}; }, a, drho, u, dT, dst, ps, cell);
+  });
 }
 
 // ---------------------------------------------------------------------------

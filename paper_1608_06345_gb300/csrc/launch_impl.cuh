@@ -24,7 +24,7 @@ cudaError_t launch_step_v(const Instance* inst, const void* src, void* dst, cons
                           bool configure_only = false) {
   const dim3 grid((unsigned)((inst->n[0] + BX - 1) / BX), (unsigned)inst->n[1], (unsigned)inst->n[2]);
   size_t smem = 0;
-  if constexpr (STAGE != 0) {
+  if constexpr (step_smem<LAT, S, STAGE, BX>() != 0) {
     smem = step_smem<LAT, S, STAGE, BX>();
     // the shared-memory opt-in is a per-device function attribute: set it
     // once per device (bit d of the mask) for this template instance
@@ -57,24 +57,39 @@ cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, cons
   return launch_step_v<LAT, S, C, STAGE, BX, MINB, false>(inst, src, dst, a, configure_only);
 }
 
+// the velocity-split step: 32 cells per block, P warps (static shared memory only)
+template <int LAT, class S, class C, int P, int MINB>
+cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, const Args<C>& a,
+                              bool configure_only = false) {
+  if (configure_only) return cudaSuccess;
+  const dim3 grid((unsigned)((inst->n[0] + 31) / 32), (unsigned)inst->n[1], (unsigned)inst->n[2]);
+  k_step_split<LAT, S, C, P, MINB><<<grid, dim3(32, P), 0, inst->stream>>>(static_cast<const S*>(src),
+                                                                           static_cast<S*>(dst), a);
+  return cudaGetLastError();
+}
+
 // Candidate shapes of the step per (lattice, storage), tried by the
 // autotuner; index 0 is the default.  (stage, cells per block, minimum
 // resident blocks per SM requested from the compiler, which caps registers):
 //   D2Q37 FP32/16-bit: (0,128,4) (0,256,2) (0,64,8) (0,128,1)
 //   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)
-//   D3Q107 FP32:       (1,64,1)  (3,64,1)  (3,64,5)  (3,64,6)  (3,128,3)
-//   D3Q107 FP64:       (1,64,1)
-//   D3Q107 16-bit:     (2,64,1)  (2,32,1)
+//   D3Q107 FP32:       (3,64,1)  (1,64,1)  (4,32,6)
+//   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)
+//   D3Q107 16-bit:     (2,64,1)  (2,32,1)  (4,32,6)
+// Stage 4 is the velocity-split step: 4 warps per block of 32 cells.  Its
+// moments are summed in another order, so its results differ from the
+// other shapes' by rounding; the defaults (index 0) are the shapes the
+// batched pool uses, whose results are bitwise those of a lone instance.
 template <int LAT, class S>
 struct StepShapes {
   static constexpr int count =
-      (LAT == 0) ? (sizeof(S) == 8 ? 3 : 4) : (sizeof(S) == 4 ? 5 : (sizeof(S) == 8 ? 1 : 2));
+      (LAT == 0) ? (sizeof(S) == 8 ? 3 : 4) : 3;
   static void get(int k, int* stage, int* bx, int* minb) {
     static const int s2[4][3] = {{0, 128, 4}, {0, 256, 2}, {0, 64, 8}, {0, 128, 1}};
     static const int s2d[3][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}};
-    static const int s3f[5][3] = {{1, 64, 1}, {3, 64, 1}, {3, 64, 5}, {3, 64, 6}, {3, 128, 3}};
-    static const int s3d[1][3] = {{1, 64, 1}};
-    static const int s3h[2][3] = {{2, 64, 1}, {2, 32, 1}};
+    static const int s3f[3][3] = {{3, 64, 1}, {1, 64, 1}, {4, 32, 6}};
+    static const int s3d[3][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}};
+    static const int s3h[3][3] = {{2, 64, 1}, {2, 32, 1}, {4, 32, 6}};
     const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : s2)
                                   : (sizeof(S) == 4 ? s3f : (sizeof(S) == 8 ? s3d : s3h));
     *stage = t[k][0];
@@ -111,17 +126,20 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
     }
   } else if constexpr (sizeof(S) == 4) {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 3, 64>(inst, src, dst, a, configure_only);
-      case 2: return launch_step_t<LAT, S, C, 3, 64, 5>(inst, src, dst, a, configure_only);
-      case 3: return launch_step_t<LAT, S, C, 3, 64, 6>(inst, src, dst, a, configure_only);
-      case 4: return launch_step_t<LAT, S, C, 3, 128, 3>(inst, src, dst, a, configure_only);
-      default: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
+      case 1: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 3, 64>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (sizeof(S) == 8) {
-    return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
+    switch (k) {
+      case 1: return launch_step_split<LAT, S, C, 4, 3>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_split<LAT, S, C, 4, 2>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
+    }
   } else {
     switch (k) {
       case 1: return launch_step_t<LAT, S, C, 2, 32>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a, configure_only);
     }
   }
@@ -153,7 +171,7 @@ cudaError_t launch_step_fd_t(const Instance* inst, const void* src, void* dst, d
 // pool: the shape of the batched step per (lattice, storage)
 template <int LAT, class S>
 struct PoolShape {
-  static constexpr int kStage = (LAT == 0) ? 0 : (sizeof(S) >= 4 ? 1 : 2);
+  static constexpr int kStage = (LAT == 0) ? 0 : (sizeof(S) == 4 ? 3 : (sizeof(S) == 8 ? 1 : 2));
   static constexpr int kBX = (LAT == 0) ? 128 : 64;
 };
 
