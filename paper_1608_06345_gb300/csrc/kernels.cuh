@@ -625,6 +625,17 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
   auto ld = [&](auto I, int plane, size_t offb) -> S {
     return ldg_s(reinterpret_cast<const S*>(sb + (size_t)plane * pb + offb));
   };
+  // address of the pulled element of direction I in plane `plane` (pair
+  // index for 16-bit storage): IDX32 -- the launcher checked that every
+  // element index of the buffer is below 2^32 -- in unsigned 32-bit element
+  // arithmetic, else plane base + 64-bit byte offset
+  auto pptr = [&](int plane, auto I) -> const char* {
+    constexpr size_t E = IsS16<S>::value ? 2 * sizeof(S) : sizeof(S);
+    if constexpr (IDX32)
+      return reinterpret_cast<const char*>(src) + (size_t)((unsigned)plane * (unsigned)ps + src_off(I)) * E;
+    else
+      return sb + (size_t)plane * ((size_t)ps * E) + (size_t)src_off(I) * E;
+  };
   if constexpr (STAGE == 0) {
     C g[Q], h[Q];
     static_for<Q>([&](auto I) {
@@ -657,15 +668,16 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     C g[Q];
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const size_t offb = (size_t)src_off(I) * sizeof(S);
       const unsigned sa = (unsigned)__cvta_generic_to_shared(sh + i * BX + t);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa),
-                   "l"(sb + (size_t)(Q + i) * pb + offb), "n"(sizeof(S)));
-      g[i] = static_cast<C>(ld(I, i, offb));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(pptr(Q + i, I)), "n"(sizeof(S)));
+      g[i] = static_cast<C>(ldg_s(reinterpret_cast<const S*>(pptr(i, I))));
     });
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    // volatile: the moments pass and the relaxation pass each read h_i from
+    // shared memory, so the 107 h values are not all held in registers
+    const volatile S* shv = sh;
     collide_store<LAT, S, C, IDX32>([&](auto I) { return g[decltype(I)::value]; },
-                             [&](auto I) { return static_cast<C>(sh[decltype(I)::value * BX + t]); }, a, dst, ps,
+                             [&](auto I) { return static_cast<C>(shv[decltype(I)::value * BX + t]); }, a, dst, ps,
                              cell);
   } else {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -673,27 +685,26 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     const int t = threadIdx.x;
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const size_t offb = (size_t)src_off(I) * sizeof(S);
       if constexpr (STAGE == 1) {
         static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
         const unsigned sa0 = (unsigned)__cvta_generic_to_shared(sg + i * BX + t);
         const unsigned sa1 = (unsigned)__cvta_generic_to_shared(sg + (Q + i) * BX + t);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa0), "l"(sb + (size_t)i * pb + offb),
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa0), "l"(pptr(i, I)), "n"(sizeof(S)));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa1), "l"(pptr(Q + i, I)),
                      "n"(sizeof(S)));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa1),
-                     "l"(sb + (size_t)(Q + i) * pb + offb), "n"(sizeof(S)));
       } else if constexpr (IsS16<S>::value) {  // the 32-bit (g_i, h_i) pair into slot [i][t]
-        reinterpret_cast<unsigned*>(smem_raw)[i * BX + t] =
-            __ldg(reinterpret_cast<const unsigned*>(src) + ((size_t)i * ps + src_off(I)));
+        reinterpret_cast<unsigned*>(smem_raw)[i * BX + t] = __ldg(reinterpret_cast<const unsigned*>(pptr(i, I)));
       } else {
-        sg[i * BX + t] = ld(I, i, offb);
-        sg[(Q + i) * BX + t] = ld(I, Q + i, offb);
+        sg[i * BX + t] = ldg_s(reinterpret_cast<const S*>(pptr(i, I)));
+        sg[(Q + i) * BX + t] = ldg_s(reinterpret_cast<const S*>(pptr(Q + i, I)));
       }
     });
     if constexpr (STAGE == 1) asm volatile("cp.async.wait_all;\n" ::: "memory");
-    // each thread reads back only the slots it filled itself
+    // each thread reads back only the slots it filled itself; the reads are
+    // volatile so that each pass re-reads shared memory instead of holding
+    // every staged value in registers
     if constexpr (IsS16<S>::value) {
-      const unsigned* sp = reinterpret_cast<const unsigned*>(smem_raw);
+      const volatile unsigned* sp = reinterpret_cast<const volatile unsigned*>(smem_raw);
       collide_store<LAT, S, C, IDX32>(
           [&](auto I) {
             float lo, hi;
@@ -707,9 +718,10 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
           },
           a, dst, ps, cell);
     } else {
+      const volatile S* sgv = sg;
       collide_store<LAT, S, C, IDX32>(
-          [&](auto I) { return raw_value<S, C>(sg[decltype(I)::value * BX + t]); },
-          [&](auto I) { return raw_value<S, C>(sg[(Q + decltype(I)::value) * BX + t]); }, a, dst, ps, cell);
+          [&](auto I) { return raw_value<S, C>(sgv[decltype(I)::value * BX + t]); },
+          [&](auto I) { return raw_value<S, C>(sgv[(Q + decltype(I)::value) * BX + t]); }, a, dst, ps, cell);
     }
   }
 }

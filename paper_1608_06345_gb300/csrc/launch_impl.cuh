@@ -45,15 +45,15 @@ cudaError_t launch_step_v(const Instance* inst, const void* src, void* dst, cons
   return cudaGetLastError();
 }
 
-// D2Q37 buffers of fewer than 2^31 elements (2Q ps) index in 32 bits, which
-// takes fewer integer instructions per load and store
+// Buffers whose element indices (2Q ps; Q ps pairs for 16-bit storage) stay
+// below 2^32 index in unsigned 32-bit arithmetic, which takes fewer integer
+// instructions per load and store (4096^2 D2Q37 and 256^3 D3Q107 both do)
 template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1>
 cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, const Args<C>& a,
                           bool configure_only = false) {
-  if constexpr (LAT == 0) {
-    if (2LL * Lat<LAT>::Q * inst->ps < (1LL << 31))
-      return launch_step_v<LAT, S, C, STAGE, BX, MINB, true>(inst, src, dst, a, configure_only);
-  }
+  const long long planes = IsS16<S>::value ? Lat<LAT>::Q : 2LL * Lat<LAT>::Q;
+  if (planes * inst->ps < (1LL << 32))
+    return launch_step_v<LAT, S, C, STAGE, BX, MINB, true>(inst, src, dst, a, configure_only);
   return launch_step_v<LAT, S, C, STAGE, BX, MINB, false>(inst, src, dst, a, configure_only);
 }
 
@@ -73,9 +73,9 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
 // resident blocks per SM requested from the compiler, which caps registers):
 //   D2Q37 FP32/16-bit: (0,128,4) (0,256,2) (0,64,8) (0,128,1)
 //   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)
-//   D3Q107 FP32:       (3,64,1)  (1,64,1)  (4,32,6)
+//   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)
 //   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)
-//   D3Q107 16-bit:     (2,64,1)  (2,32,1)  (4,32,6)
+//   D3Q107 16-bit:     (2,64,8)  (2,64,1)  (2,32,1)  (4,32,6)
 // Stage 4 is the velocity-split step: 4 warps per block of 32 cells.  Its
 // moments are summed in another order, so its results differ from the
 // other shapes' by rounding; the defaults (index 0) are the shapes the
@@ -83,13 +83,13 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
 template <int LAT, class S>
 struct StepShapes {
   static constexpr int count =
-      (LAT == 0) ? (sizeof(S) == 8 ? 3 : 4) : 3;
+      (LAT == 0) ? (sizeof(S) == 8 ? 3 : 4) : (sizeof(S) == 8 ? 3 : 4);
   static void get(int k, int* stage, int* bx, int* minb) {
     static const int s2[4][3] = {{0, 128, 4}, {0, 256, 2}, {0, 64, 8}, {0, 128, 1}};
     static const int s2d[3][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}};
-    static const int s3f[3][3] = {{3, 64, 1}, {1, 64, 1}, {4, 32, 6}};
+    static const int s3f[4][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}};
     static const int s3d[3][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}};
-    static const int s3h[3][3] = {{2, 64, 1}, {2, 32, 1}, {4, 32, 6}};
+    static const int s3h[4][3] = {{2, 64, 8}, {2, 64, 1}, {2, 32, 1}, {4, 32, 6}};
     const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : s2)
                                   : (sizeof(S) == 4 ? s3f : (sizeof(S) == 8 ? s3d : s3h));
     *stage = t[k][0];
@@ -126,9 +126,10 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
     }
   } else if constexpr (sizeof(S) == 4) {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
-      case 2: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
-      default: return launch_step_t<LAT, S, C, 3, 64>(inst, src, dst, a, configure_only);
+      case 1: return launch_step_t<LAT, S, C, 3, 64>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
+      case 3: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 3, 64, 6>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (sizeof(S) == 8) {
     switch (k) {
@@ -138,9 +139,10 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
     }
   } else {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 2, 32>(inst, src, dst, a, configure_only);
-      case 2: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
-      default: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a, configure_only);
+      case 1: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_t<LAT, S, C, 2, 32>(inst, src, dst, a, configure_only);
+      case 3: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 2, 64, 8>(inst, src, dst, a, configure_only);
     }
   }
 }

@@ -1,6 +1,7 @@
 """Parity at full size, in the launch configuration bench.py times (autotuned
 shape): 4096^2 D2Q37 (FP32 and FP16 storage) and 256^3 D3Q107 FP32, seeded
-Fourier fields.
+Fourier fields; and 272^3 D3Q107 FP32, whose element indices exceed 2^32
+(the 64-bit addressing path).
 
 The oracle cannot step these grids in a test, so it checks sampled cells one
 by one: after k steps a cell depends only on the cells within 3k of it, so
@@ -37,12 +38,13 @@ def patch(field, shape, center, radius):
     return one(field)
 
 
-def sampled_parity(lat, shape, fields, prec, gamma, tau_f, tau_g, tol, seed=0):
+def sampled_parity(lat, shape, fields, prec, gamma, tau_f, tau_g, tol, seed=0, tune=True):
     from paper_1608_06345_gb300 import autotune, lbm
     D = len(shape)
     s = lbm.Solver(lat, gamma, tau_f, tau_g, shape, prec=prec)
     s.init(*fields)
-    autotune.tune(s, reps=2, cache_path=None)
+    if tune:
+        autotune.tune(s, reps=2, cache_path=None)
     s.step(K)
     rho, u, T = s.moments()
     c_before = None
@@ -99,4 +101,21 @@ def test_d3q107_fp32_256():
     s.sync()
     assert abs(c1[0] - c0[0]) / c0[0] <= 4 * 100 * 2.0 ** -24
     assert abs(c1[-1] - c0[-1]) / c0[-1] <= 4 * 100 * 2.0 ** -24  # tau_f = tau_g: energy too
+    s.close()
+
+
+def test_d3q107_fp32_272_indexes_in_64_bits():
+    """272^3 cells: 2Q ps = 214 x 20,123,648 = 4.31e9 element indices, above
+    2^32, so the step takes its 64-bit addressing path (below 2^32 it indexes
+    in 32 bits).  Default shape, sampled parity and conserved totals."""
+    shape = (272, 272, 272)
+    assert 2 * 107 * 272 ** 3 > 2 ** 32
+    fields = li.fourier_fields(shape, seed_u=3, seed_rho=4, seed_T=5)
+    s = sampled_parity(1, shape, fields, 1, 1.4, 0.6, 0.6, TOL["f32"], seed=1, tune=False)
+    c0 = s.conserved()
+    s.step(7)
+    c1 = s.conserved()
+    s.sync()
+    assert abs(c1[0] - c0[0]) / c0[0] <= 4 * 10 * 2.0 ** -24
+    assert abs(c1[-1] - c0[-1]) / c0[-1] <= 4 * 10 * 2.0 ** -24
     s.close()
