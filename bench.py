@@ -90,6 +90,9 @@ WORKLOADS = {
     "periodic3d_f64_small": dict(lattice=1, prec="f64", shape=(64, 64, 64), gamma=1.4, tau_f=0.6, tau_g=0.6,
                                  steps=4, fields="fourier3d",
                                  desc="D3Q107 FP64 periodic 64^3 (profiling case, 0.9 GB state > L2), 4 steps"),
+    "periodic3d_s16f": dict(lattice=1, prec="f32_s16f", shape=(256, 256, 256), gamma=1.4, tau_f=0.6, tau_g=0.6,
+                            steps=100, fields="fourier3d",
+                            desc="D3Q107 FP32 compute, FP16 deviation storage, periodic 256^3, 100 steps per solve"),
     "periodic3d": dict(lattice=1, prec="f32", shape=(256, 256, 256), gamma=1.4, tau_f=0.6, tau_g=0.6, steps=100,
                        fields="fourier3d",
                        desc="D3Q107 FP32 periodic 256^3, 8-mode Fourier rho/u/T (seeds 3,4,5), gamma 1.4, "

@@ -191,8 +191,10 @@ int lbm_conserved_noalloc(int lattice, int prec, double gamma, double rho0, doub
 /* Launch shapes of the step kernel.  Each (lattice, precision) has a small
  * table of compiled candidates (how the pulled values are staged --
  * registers, shared memory by cp.async, g in registers and h in shared
- * memory (stages 0-3), or the velocities of each cell split over 4 warps
- * (stage 4) -- and the cells per thread block); index 0 is the default.
+ * memory (stages 0-3), the velocities of each cell split over 4 warps
+ * (stage 4), or, for 16-bit storage, the (g, h) pairs held packed in
+ * registers (stage 6) -- and the cells per thread block); index 0 is the
+ * default.
  * lbm_shape_info describes candidate `index` (LBM_EINVAL past the end). */
 int lbm_shape_info(int lattice, int prec, int index, int* stage, int* block);
 

@@ -595,6 +595,9 @@ __device__ __forceinline__ C raw_value(S v) {
 //   STAGE 2: staged in shared memory by plain loads (D3Q107, 16-bit storage)
 //   STAGE 3: g in registers, h staged in shared memory by cp.async (D3Q107,
 //            FP32/FP64): half the shared memory per cell of STAGE 1
+//   STAGE 6: 16-bit storage, the Q pulled (g_i, h_i) pairs held packed in
+//            registers (one register per direction, half of STAGE 0's) and
+//            unpacked where each pass uses them
 // A block covers BX consecutive cells of a row (thread = cell).
 // ---------------------------------------------------------------------------
 template <int LAT, class S, class C, int STAGE, int BX, bool IDX32 = false>
@@ -660,6 +663,33 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     });
     collide_store<LAT, S, C, IDX32>([&](auto I) { return g[decltype(I)::value]; },
                              [&](auto I) { return h[decltype(I)::value]; }, a, dst, ps, cell);
+  } else if constexpr (STAGE == 6) {
+    static_assert(IsS16<S>::value, "packed pairs need 16-bit storage");
+    unsigned pr[Q];
+    static_for<Q>([&](auto I) {
+      pr[decltype(I)::value] = __ldg(reinterpret_cast<const unsigned*>(pptr(decltype(I)::value, I)));
+    });
+    auto lo = [](unsigned v) -> C {
+      float l, h;
+      unpack16<S>(v, l, h);
+      return static_cast<C>(l);
+    };
+    auto hi = [](unsigned v) -> C {
+      float l, h;
+      unpack16<S>(v, l, h);
+      return static_cast<C>(h);
+    };
+    C drho, u[3], dT;
+    moments_raw<LAT, C, true>([&](auto I) { return lo(pr[decltype(I)::value]); },
+                              [&](auto I) { return hi(pr[decltype(I)::value]); }, a, drho, u, dT);
+    if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+    // an empty asm that claims to change each pair: the relaxation pass
+    // unpacks again instead of the compiler keeping the moments pass's 2Q
+    // unpacked values alive (it emits no instruction)
+    static_for<Q>([&](auto I) { asm volatile("" : "+r"(pr[decltype(I)::value])); });
+    relax_store<LAT, S, C, IDX32, false>([&](auto I) { return lo(pr[decltype(I)::value]); },
+                                         [&](auto I) { return hi(pr[decltype(I)::value]); },
+                                         [](auto) { return ConvGH<C>{C(0), C(0)}; }, a, drho, u, dT, dst, ps, cell);
   } else if constexpr (STAGE == 3) {
     static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
     extern __shared__ __align__(16) unsigned char smem_raw[];

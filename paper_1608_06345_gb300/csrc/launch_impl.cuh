@@ -12,11 +12,11 @@ const Args<C>& args_of(const Instance* inst) {
   else return inst->af;
 }
 
-// dynamic shared memory of a step shape: none (STAGE 0), h only (STAGE 3),
+// dynamic shared memory of a step shape: none (STAGE 0, 6), h only (STAGE 3),
 // g and h (STAGE 1, 2)
 template <int LAT, class S, int STAGE, int BX>
 constexpr size_t step_smem() {
-  return STAGE == 0 ? 0 : (STAGE == 3 ? 1 : 2) * sizeof(S) * Lat<LAT>::Q * BX;
+  return (STAGE == 0 || STAGE == 6) ? 0 : (STAGE == 3 ? 1 : 2) * sizeof(S) * Lat<LAT>::Q * BX;
 }
 
 template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false>
@@ -71,11 +71,12 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
 // Candidate shapes of the step per (lattice, storage), tried by the
 // autotuner; index 0 is the default.  (stage, cells per block, minimum
 // resident blocks per SM requested from the compiler, which caps registers):
-//   D2Q37 FP32/16-bit: (0,128,4) (0,256,2) (0,64,8) (0,128,1)
+//   D2Q37 FP32:        (0,128,4) (0,256,2) (0,64,8) (0,128,1)
+//   D2Q37 16-bit:      (6,128,8) (6,128,7) (6,128,6) (6,256,3) (0,128,4) (0,64,8)
 //   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)
 //   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)
 //   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)
-//   D3Q107 16-bit:     (2,64,8)  (2,64,1)  (2,32,1)  (4,32,6)
+//   D3Q107 16-bit:     (6,64,6)  (2,64,8)  (2,64,1)  (4,32,6)
 // Stage 4 is the velocity-split step: 4 warps per block of 32 cells.  Its
 // moments are summed in another order, so its results differ from the
 // other shapes' by rounding; the defaults (index 0) are the shapes the
@@ -83,14 +84,15 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
 template <int LAT, class S>
 struct StepShapes {
   static constexpr int count =
-      (LAT == 0) ? (sizeof(S) == 8 ? 3 : 4) : (sizeof(S) == 8 ? 3 : 4);
+      (LAT == 0) ? (sizeof(S) == 8 ? 3 : (sizeof(S) == 2 ? 6 : 4)) : (sizeof(S) == 8 ? 3 : 4);
   static void get(int k, int* stage, int* bx, int* minb) {
     static const int s2[4][3] = {{0, 128, 4}, {0, 256, 2}, {0, 64, 8}, {0, 128, 1}};
+    static const int s2h[6][3] = {{6, 128, 8}, {6, 128, 7}, {6, 128, 6}, {6, 256, 3}, {0, 128, 4}, {0, 64, 8}};
     static const int s2d[3][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}};
     static const int s3f[4][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}};
     static const int s3d[3][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}};
-    static const int s3h[4][3] = {{2, 64, 8}, {2, 64, 1}, {2, 32, 1}, {4, 32, 6}};
-    const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : s2)
+    static const int s3h[4][3] = {{6, 64, 6}, {2, 64, 8}, {2, 64, 1}, {4, 32, 6}};
+    const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : (sizeof(S) == 2 ? s2h : s2))
                                   : (sizeof(S) == 4 ? s3f : (sizeof(S) == 8 ? s3d : s3h));
     *stage = t[k][0];
     *bx = t[k][1];
@@ -117,6 +119,15 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
       case 2: return launch_step_t<LAT, S, C, 0, 64>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a, configure_only);
     }
+  } else if constexpr (LAT == 0 && sizeof(S) == 2) {
+    switch (k) {
+      case 1: return launch_step_t<LAT, S, C, 6, 128, 7>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_t<LAT, S, C, 6, 128, 6>(inst, src, dst, a, configure_only);
+      case 3: return launch_step_t<LAT, S, C, 6, 256, 3>(inst, src, dst, a, configure_only);
+      case 4: return launch_step_t<LAT, S, C, 0, 128, 4>(inst, src, dst, a, configure_only);
+      case 5: return launch_step_t<LAT, S, C, 0, 64, 8>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 6, 128, 8>(inst, src, dst, a, configure_only);
+    }
   } else if constexpr (LAT == 0) {
     switch (k) {
       case 1: return launch_step_t<LAT, S, C, 0, 256, 2>(inst, src, dst, a, configure_only);
@@ -139,10 +150,10 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
     }
   } else {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a, configure_only);
-      case 2: return launch_step_t<LAT, S, C, 2, 32>(inst, src, dst, a, configure_only);
+      case 1: return launch_step_t<LAT, S, C, 2, 64, 8>(inst, src, dst, a, configure_only);
+      case 2: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a, configure_only);
       case 3: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
-      default: return launch_step_t<LAT, S, C, 2, 64, 8>(inst, src, dst, a, configure_only);
+      default: return launch_step_t<LAT, S, C, 6, 64, 6>(inst, src, dst, a, configure_only);
     }
   }
 }
