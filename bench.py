@@ -68,6 +68,9 @@ WORKLOADS = {
                  fields="fourier2d", scheme="fd", lam=0.03,
                  desc="D2Q37 FP32 finite-difference variant (Sec. III, third-order upwind, lambda 0.03), periodic "
                       "4096x4096, recipe fields, 200 steps per solve"),
+    "fd2d_small": dict(lattice=0, prec="f32", shape=(1024, 1024), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=20,
+                       fields="fourier2d", scheme="fd", lam=0.03,
+                       desc="D2Q37 FP32 finite-difference variant, periodic 1024x1024 (profiling case), 20 steps"),
     "periodic2d_small": dict(lattice=0, prec="f32", shape=(1024, 1024), gamma=1.4, tau_f=0.55, tau_g=0.7, steps=20,
                              fields="fourier2d",
                              desc="D2Q37 FP32 periodic 1024x1024 (profiling case, 0.6 GB state > L2), 20 steps"),
