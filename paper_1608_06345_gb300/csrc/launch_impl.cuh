@@ -2,6 +2,8 @@
 // one (lattice, storage type, compute type).
 #pragma once
 
+#include <atomic>
+
 #include "runtime.h"
 
 namespace lbm {
@@ -27,16 +29,18 @@ cudaError_t launch_step_v(const Instance* inst, const void* src, void* dst, cons
   if constexpr (step_smem<LAT, S, STAGE, BX>() != 0) {
     smem = step_smem<LAT, S, STAGE, BX>();
     // the shared-memory opt-in is a per-device function attribute: set it
-    // once per device (bit d of the mask) for this template instance
-    static unsigned long long configured = 0;
+    // once per device (bit d of the mask) for this template instance; the
+    // mask is atomic because host threads may launch concurrently (setting
+    // the attribute twice is harmless)
+    static std::atomic<unsigned long long> configured{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(configured & (1ull << dev))) {
+    if (dev >= 64 || !(configured.load(std::memory_order_acquire) & (1ull << dev))) {
       e = cudaFuncSetAttribute(k_step<LAT, S, C, STAGE, BX, MINB, IDX32>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      if (dev < 64) configured |= (1ull << dev);
+      if (dev < 64) configured.fetch_or(1ull << dev, std::memory_order_release);
     }
   }
   if (configure_only) return cudaSuccess;
