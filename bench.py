@@ -230,6 +230,41 @@ def cpu_oracle_sample(wl, seconds_target=15.0, min_steps=1):
     return mlups, ora.get_threads(), desc
 
 
+def cpu_oracle_single_core(wl, seconds_target=5.0):
+    """The oracle on one host core, on a quarter-size box (512^2 / 48^3) of the
+    same recipe.  Returns (MLUPS, description)."""
+    from oracle import oracle as ora
+    keep = ora.get_threads()
+    ora.set_threads(1)
+    try:
+        shape = (512, 512) if len(wl["shape"]) == 2 else (48, 48, 48)
+        rho, u, T = make_fields(wl, shape)
+        s = ora.Oracle(wl["lattice"], wl["gamma"], wl["tau_f"], wl["tau_g"], shape)
+        s.init(rho, u, T)
+        t0 = time.perf_counter()
+        s.step(1)
+        one = time.perf_counter() - t0
+        steps = max(1, int(seconds_target / max(one, 1e-6)))
+        t0 = time.perf_counter()
+        s.step(steps)
+        dt = time.perf_counter() - t0
+    finally:
+        ora.set_threads(keep)
+    return int(np.prod(shape)) * steps / dt / 1e6, f"{'x'.join(map(str, shape))} box, {steps} steps, 1 thread"
+
+
+def cpu_model():
+    """Host CPU model name as lscpu reports it (empty if unavailable)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return ""
+    for line in out.splitlines():
+        if line.strip().startswith("Model name"):
+            return line.split(":", 1)[1].strip()
+    return ""
+
+
 def run_reference(args, wl):
     """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
     world, rank, _ = dist_info()
@@ -390,7 +425,10 @@ def run_ours(args, wl):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, cores, desc = cpu_oracle_sample(wl, seconds_target=args.cpu_seconds)
-        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+        v1, desc1 = cpu_oracle_single_core(wl)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc,
+               "single_core": {"value": v1, "unit": "MLUPS", "sample": desc1}, "cpu_model": cpu_model(),
+               "nproc": os.cpu_count()}
 
     line = {
         "metric": "MLUPS (f+g)", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
