@@ -77,7 +77,7 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
 // resident blocks per SM requested from the compiler, which caps registers):
 //   D2Q37 FP32:        (0,128,4) (0,256,2) (0,64,8) (0,128,1)
 //   D2Q37 16-bit:      (6,128,8) (6,128,7) (6,128,6) (6,256,3) (0,128,4) (0,64,8)
-//   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)
+//   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)  (4,32,4)
 //   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)
 //   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)
 //   D3Q107 16-bit:     (6,64,6)  (2,64,8)  (2,64,1)  (4,32,6)
@@ -88,11 +88,11 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
 template <int LAT, class S>
 struct StepShapes {
   static constexpr int count =
-      (LAT == 0) ? (sizeof(S) == 8 ? 3 : (sizeof(S) == 2 ? 6 : 4)) : (sizeof(S) == 8 ? 3 : 4);
+      (LAT == 0) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 2 ? 6 : 4)) : (sizeof(S) == 8 ? 3 : 4);
   static void get(int k, int* stage, int* bx, int* minb) {
     static const int s2[4][3] = {{0, 128, 4}, {0, 256, 2}, {0, 64, 8}, {0, 128, 1}};
     static const int s2h[6][3] = {{6, 128, 8}, {6, 128, 7}, {6, 128, 6}, {6, 256, 3}, {0, 128, 4}, {0, 64, 8}};
-    static const int s2d[3][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}};
+    static const int s2d[4][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}, {4, 32, 4}};
     static const int s3f[4][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}};
     static const int s3d[3][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}};
     static const int s3h[4][3] = {{6, 64, 6}, {2, 64, 8}, {2, 64, 1}, {4, 32, 6}};
@@ -121,6 +121,7 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
     switch (k) {
       case 1: return launch_step_t<LAT, S, C, 0, 256>(inst, src, dst, a, configure_only);
       case 2: return launch_step_t<LAT, S, C, 0, 64>(inst, src, dst, a, configure_only);
+      case 3: return launch_step_split<LAT, S, C, 4, 4>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (LAT == 0 && sizeof(S) == 2) {
