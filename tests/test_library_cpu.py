@@ -116,3 +116,13 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_sync(None) == lbm.LBM_EINVAL
     assert "NULL" in lbm.lbm_last_error()
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """There is no CPU fallback: without the compiled library the binding
+    raises instead of computing anything on the host."""
+    from paper_1608_06345_gb300 import lbm
+    monkeypatch.setattr(lbm, "_lib", None)
+    monkeypatch.setattr(lbm, "library_path", lambda: os.path.join(os.path.dirname(__file__), "no_such_liblbm.so"))
+    with pytest.raises(ImportError, match="not built"):
+        lbm.load()
