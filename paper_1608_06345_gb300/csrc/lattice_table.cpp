@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <vector>
 
 #include "lattice.h"
@@ -101,7 +102,7 @@ bool weights_for(const Problem& P, double r, double* w, double* resid) {
 
 }  // namespace
 
-int build_lattice_table(int lattice, LatticeTable* out) {
+static int build_lattice_table_uncached(int lattice, LatticeTable* out) {
   Problem P{};
   if (lattice == 0) {
     static const int m[9][3] = {{0, 0, 0}, {2, 0, 0}, {4, 0, 0}, {2, 2, 0}, {6, 0, 0},
@@ -282,6 +283,19 @@ int hermite_quadrature(int D, int G, const int* reps, int nconds, const int* exp
   if (r_out) *r_out = r;
   if (max_residual) *max_residual = worst;
   return 0;
+}
+
+// The refinement depends only on the lattice: it is solved once per lattice
+// per process, and every instance, pool submission and no-allocation
+// reduction copies the result.
+int build_lattice_table(int lattice, LatticeTable* out) {
+  if (lattice != 0 && lattice != 1) return -1;
+  static std::once_flag once[2];
+  static LatticeTable table[2];
+  static int status[2];
+  std::call_once(once[lattice], [lattice] { status[lattice] = build_lattice_table_uncached(lattice, &table[lattice]); });
+  if (status[lattice] == 0) *out = table[lattice];
+  return status[lattice];
 }
 
 }  // namespace lbm

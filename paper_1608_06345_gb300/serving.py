@@ -84,24 +84,31 @@ def serve(requests, arrivals, backend, clock=time.perf_counter, keep_results=Fal
     order = np.argsort(arrivals, kind="stable")
     pending = deque((float(arrivals[i]), requests[i]) for i in order)
     records = {r.rid: Record(r.rid, float(a)) for r, a in zip(requests, arrivals)}
+    # queue: refused since room last freed up; fresh: arrived, not yet tried.
+    # A refused submission changes nothing and room frees only when results
+    # are read, so queued requests are retried only after that.
     queue = deque()
+    fresh = deque()
+    freed = False
     active = {}
     t0 = clock()
-    while pending or queue or active:
+    while pending or queue or fresh or active:
         now = clock() - t0
         while pending and pending[0][0] <= now:
-            queue.append(pending.popleft()[1])
-        # admission: arrival order; later requests may pass one that does not fit yet
+            fresh.append(pending.popleft()[1])
+        # admission in arrival order; later requests may pass one that does not fit yet
+        candidates = (queue + fresh) if freed else fresh
         still = deque()
-        while queue:
-            req = queue.popleft()
+        for req in candidates:
             ticket = backend.submit(req)
             if ticket is None:
                 still.append(req)
             else:
                 active[ticket] = req
                 records[req.rid].admitted = clock() - t0
-        queue = still
+        queue = still if freed else queue + still
+        fresh = deque()
+        freed = False
         if active:
             backend.run_bundle()
             finished = [t for t in active if backend.done(t)]
@@ -113,6 +120,7 @@ def serve(requests, arrivals, backend, clock=time.perf_counter, keep_results=Fal
                 rec.status = status
                 if keep_results:
                     rec.result = res
+            freed = freed or bool(finished)
         elif pending and not queue:
             wait = pending[0][0] - (clock() - t0)
             if wait > 0:

@@ -93,3 +93,37 @@ def test_shock_tube_request_recipe():
         # geometric normalisation of the density and pressure ratios
         assert abs(p["left"][0] * p["right"][0] - 1.0) < 1e-12
         assert abs(p["left"][0] * p["left"][2] * p["right"][0] * p["right"][2] - 1.0) < 1e-12
+
+
+class CountingPool(FakePool):
+    """FakePool that fails the test if a request is refused twice with no
+    result read in between (a refusal changes nothing, and room only frees
+    when results are read, so such a retry is wasted work)."""
+
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self.generation = 0
+        self.refused_at = {}
+        self.attempts = 0
+
+    def submit(self, req):
+        self.attempts += 1
+        t = super().submit(req)
+        if t is None:
+            assert self.refused_at.get(req.rid) != self.generation, f"request {req.rid} retried with no room freed"
+            self.refused_at[req.rid] = self.generation
+        return t
+
+    def result(self, t, req):
+        self.generation += 1
+        return super().result(t, req)
+
+
+def test_refused_requests_wait_for_freed_room():
+    reqs = make_requests(60, seed=4)
+    pool = CountingPool(budget_cells=500, bundle_steps=25)
+    recs = serving.serve(reqs, np.zeros(len(reqs)), pool, idle_sleep=0)
+    assert all(r.status == "ok" for r in recs)
+    assert pool.peak <= 500
+    # every attempt is either an admission or a refusal in a fresh generation
+    assert pool.attempts <= len(reqs) * (pool.generation + 1)
