@@ -56,14 +56,34 @@ class Record:
 
 
 class PoolBackend:
-    """Backend of the loop on the GPU pool (paper_1608_06345_gb300.lbm.Pool)."""
+    """Backend of the loop on the GPU pool (paper_1608_06345_gb300.lbm.Pool).
+
+    It mirrors the pool's byte accounting (an admission takes
+    lbm_pool_instance_bytes, reading its result gives them back) and refuses
+    a request larger than the free total without calling the library: no
+    layout of the arena could hold it, so the pool would refuse it too."""
 
     def __init__(self, pool):
         self.pool = pool
+        st = pool.stats()
+        self.used, self.arena = int(st["bytes_used"]), int(st["bytes_budget"])
+        self._bytes = {}
+
+    def _need(self, req):
+        b = self._bytes.get(req.rid)
+        if b is None:
+            b = self._bytes[req.rid] = int(self.pool.instance_bytes(req.shape))
+        return b
 
     def submit(self, req):
-        return self.pool.submit(req.gamma, req.tau_f, req.tau_g, req.shape, req.bc, req.fields, req.steps,
-                                rho0=req.rho0, T0=req.T0)
+        need = self._need(req)
+        if self.used + need > self.arena:
+            return None
+        t = self.pool.submit(req.gamma, req.tau_f, req.tau_g, req.shape, req.bc, req.fields, req.steps,
+                             rho0=req.rho0, T0=req.T0)
+        if t is not None:
+            self.used += need
+        return t
 
     def run_bundle(self):
         self.pool.run(1)
@@ -75,6 +95,7 @@ class PoolBackend:
     def result(self, ticket, req):
         from . import lbm
         rc, fields = self.pool.result(ticket, req.cells)
+        self.used -= self._need(req)
         return ("ok" if rc == lbm.LBM_OK else "nonfinite"), fields
 
 
