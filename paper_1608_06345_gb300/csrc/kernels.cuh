@@ -20,9 +20,10 @@
 // sum href = rho0 delta T0 / 2).  Working on the small dg, dh keeps FP32 and
 // 16-bit storage from losing the momentum to cancellation in sum xi_i g_i.
 //
-// Storage: structure of arrays, plane p (0..Q-1 for g, Q..2Q-1 for h) of N
-// cells at offset p * ps elements, cell index x + nx*(y + ny*z).  FP64/FP32
-// planes hold dg, dh; 16-bit planes hold dg/gref and dh/hscale.
+// Storage: structure of arrays, cell index x + nx*(y + ny*z).  FP64/FP32:
+// 2Q planes (0..Q-1 for g, Q..2Q-1 for h) of ps elements holding dg, dh.
+// 16-bit: Q planes of ps 32-bit pairs, g_i in the low half and h_i in the
+// high half, holding dg/gref and dh/hscale.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -507,8 +508,9 @@ __device__ __forceinline__ void relax_store(GetG&& getg, GetH&& geth, Conv&& con
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
   constexpr bool SCALED = IsS16<S>::value;
-  // IDX32: element index plane * ps + cell in 32 bits (the caller checked
-  // that 2Q ps < 2^31); else plane base + the cell's byte offset in 64 bits
+  // IDX32: element index plane * ps + cell in unsigned 32 bits (the caller
+  // checked that every element index is below 2^32); else plane base + the
+  // cell's byte offset in 64 bits
   char* db = reinterpret_cast<char*>(dst) + (size_t)cell * sizeof(S);
   const size_t pb = (size_t)ps * sizeof(S);
   auto st = [&](int plane, S v) {
