@@ -252,9 +252,12 @@ size_t lbm_pool_instance_bytes(lbm_pool_handle p, const lbm_grid* grid);
 /* Admit an instance: validate as lbm_create (grid->prec must equal the
  * pool's; grid->stream and grid->device_mem are ignored), set it to the
  * equilibrium of the host fields rho, u, T (as lbm_init) and give it `steps`
- * time steps to take.  Synchronises the pool stream (the host arrays are
- * copied when it returns).  LBM_EBUSY if no slot, budget or work-list room
- * is free now (nothing changes; retry after results are read). */
+ * time steps to take from the next lbm_pool_run on.  May be called while a
+ * bundle runs: the copies and the initialisation use the pool's own
+ * admission stream, which it synchronises (the host arrays are copied when
+ * it returns), not the pool stream.  LBM_EBUSY if no slot, budget or
+ * work-list room is free now (nothing changes; retry after results are
+ * read). */
 int lbm_pool_submit(lbm_pool_handle p, double gamma, double tau_f, double tau_g, const lbm_grid* grid,
                     const double* rho, const double* u, const double* T, long steps, long long* ticket);
 

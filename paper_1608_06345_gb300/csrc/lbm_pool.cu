@@ -10,6 +10,13 @@
 // CUDA graph; between bundles the host admits and retires instances by
 // editing the slot table and the tile list, which the graph reads from
 // device memory.
+//
+// Admissions may overlap a running bundle: the fields are copied and the
+// instance initialised on a second (io) stream, in arena memory and a slot
+// that no resident instance uses, and its error word is cleared there (only
+// kernels of instances with steps left write error words).  The slot
+// descriptor is written on the pool stream at the next lbm_pool_run, because
+// the bundle's advance kernel walks every slot descriptor.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,6 +34,8 @@ namespace {
 
 struct Slot {
   bool used = false;
+  bool desc_pending = false;  // descriptor not yet in device memory (written by the next run)
+  alignas(16) unsigned char desc[sizeof(PoolSlot<double>)];
   long long ticket = -1;
   size_t off = 0, bytes = 0;  // arena range
   Instance inst;              // geometry, constants, buffers
@@ -52,6 +61,8 @@ struct lbm_pool {
   int lattice = 0, prec = 0, D = 2, Q = 37;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t io = nullptr;      // admissions (may overlap a running bundle)
+  cudaEvent_t io_done = nullptr;  // recorded after the admissions' work
   unsigned char* mem = nullptr;
   bool own_mem = false;
   unsigned char* arena = nullptr;
@@ -200,7 +211,10 @@ int build_graph(lbm_pool* p) {
 }
 
 void release(lbm_pool* p) {
+  if (p->io) cudaStreamSynchronize(p->io);
   if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->io_done) cudaEventDestroy(p->io_done);
+  if (p->io) cudaStreamDestroy(p->io);
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->own_mem && p->mem) cudaFree(p->mem);
@@ -253,6 +267,14 @@ int lbm_pool_create(lbm_pool_handle* out, const lbm_pool_config* cfg) {
       return set_error(LBM_ECUDA, std::string("creating the pool stream: ") + cudaGetErrorString(e));
     }
     p->own_stream = true;
+  }
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&p->io, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->io_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      release(p);
+      return set_error(LBM_ECUDA, std::string("creating the admission stream: ") + cudaGetErrorString(e));
+    }
   }
   if (cfg->device_mem) {
     if (cfg->device_bytes < l.total) {
@@ -348,30 +370,32 @@ int lbm_pool_submit(lbm_pool_handle p, double gamma, double tau_f, double tau_g,
   I.red_partial = nullptr;
   fill_instance_args(&I);
 
-  // fields -> the idle buffer -> equilibrium in buffer 0
+  // fields -> the idle buffer -> equilibrium in buffer 0, on the io stream
+  // (this memory and this slot are not touched by a bundle in flight)
+  I.stream = p->io;
   cudaError_t e = cudaSuccess;
   if (I.N > 0) {
     double* st = static_cast<double*>(I.buf[1]);
     const size_t nb = sizeof(double) * (size_t)I.N;
-    e = cudaMemcpyAsync(st, rho, nb, cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(st + I.N, u, nb * I.D, cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(st + (1 + I.D) * I.N, T, nb, cudaMemcpyHostToDevice, p->stream);
+    e = cudaMemcpyAsync(st, rho, nb, cudaMemcpyHostToDevice, p->io);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st + I.N, u, nb * I.D, cudaMemcpyHostToDevice, p->io);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st + (1 + I.D) * I.N, T, nb, cudaMemcpyHostToDevice, p->io);
     if (e == cudaSuccess) e = p->L->init(&I, I.buf[0], st, st + I.N, st + (1 + I.D) * I.N);
   }
-  alignas(16) unsigned char desc[sizeof(PoolSlot<double>)];
-  if (p->prec == kF64) make_slot_desc<double>(I, steps, reinterpret_cast<PoolSlot<double>*>(desc));
-  else make_slot_desc<float>(I, steps, reinterpret_cast<PoolSlot<float>*>(desc));
-  const size_t dsz = (p->prec == kF64) ? sizeof(PoolSlot<double>) : sizeof(PoolSlot<float>);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_slots + (size_t)s * p->slot_size, desc, dsz, cudaMemcpyHostToDevice,
-                                            p->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_flags + s, 0, sizeof(unsigned int), p->stream);
-  // host fields and the descriptor must outlive the copies
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_flags + s, 0, sizeof(unsigned int), p->io);
+  if (e == cudaSuccess) e = cudaEventRecord(p->io_done, p->io);
+  // the host fields must outlive the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->io);
+  I.stream = p->stream;
   if (e != cudaSuccess) {
     arena_free(p, off, bytes);
     return set_error(LBM_ECUDA, std::string("admitting an instance: ") + cudaGetErrorString(e));
   }
   Slot& sl = p->slots[s];
+  std::memset(sl.desc, 0, sizeof(sl.desc));
+  if (p->prec == kF64) make_slot_desc<double>(I, steps, reinterpret_cast<PoolSlot<double>*>(sl.desc));
+  else make_slot_desc<float>(I, steps, reinterpret_cast<PoolSlot<float>*>(sl.desc));
+  sl.desc_pending = true;
   sl.used = true;
   sl.ticket = p->next_ticket++;
   sl.off = off;
@@ -391,6 +415,23 @@ int lbm_pool_run(lbm_pool_handle p, int bundles) {
   if (!p) return set_error(LBM_EINVAL, "pool is NULL");
   if (bundles < 0) return set_error(LBM_EINVAL, "bundles must be >= 0");
   for (int b = 0; b < bundles; ++b) {
+    bool pending = false;
+    for (const Slot& sl : p->slots) pending = pending || (sl.used && sl.desc_pending);
+    if (pending) {
+      // the admissions' initialisation precedes the bundle; the descriptors
+      // are written between bundles, on the pool stream
+      cudaError_t e = cudaStreamWaitEvent(p->stream, p->io_done, 0);
+      for (int s = 0; s < p->max_slots && e == cudaSuccess; ++s) {
+        Slot& sl = p->slots[s];
+        if (!sl.used || !sl.desc_pending) continue;
+        e = cudaMemcpyAsync(p->d_slots + (size_t)s * p->slot_size, sl.desc, p->slot_size, cudaMemcpyHostToDevice,
+                            p->stream);
+        sl.desc_pending = false;
+      }
+      if (e != cudaSuccess)
+        return set_error(LBM_ECUDA, std::string("writing slot descriptors: ") + cudaGetErrorString(e));
+      p->tiles_dirty = true;  // upload_tiles synchronises the pool stream: the descriptor sources stay valid
+    }
     if (p->tiles_dirty) {
       int rc = upload_tiles(p);
       if (rc != LBM_OK) return rc;

@@ -85,9 +85,15 @@ class PoolBackend:
             self.used += need
         return t
 
-    def run_bundle(self):
+    def launch_bundle(self):
         self.pool.run(1)
+
+    def wait_bundle(self):
         self.pool.sync()
+
+    def run_bundle(self):
+        self.launch_bundle()
+        self.wait_bundle()
 
     def done(self, ticket):
         return self.pool.poll(ticket)[0]
@@ -101,10 +107,16 @@ class PoolBackend:
 
 def serve(requests, arrivals, backend, clock=time.perf_counter, keep_results=False, idle_sleep=1e-4):
     """Run the continuous-batching loop.  `arrivals[i]` is request i's arrival
-    time in seconds from the start.  Returns one Record per request."""
+    time in seconds from the start.  Returns one Record per request.
+
+    Each iteration launches a step bundle for everything resident, admits
+    arrived requests while it runs (backend.launch_bundle / wait_bundle; a
+    backend with only run_bundle admits between bundles instead), waits for
+    it and reads back the finished instances."""
     order = np.argsort(arrivals, kind="stable")
     pending = deque((float(arrivals[i]), requests[i]) for i in order)
     records = {r.rid: Record(r.rid, float(a)) for r, a in zip(requests, arrivals)}
+    overlap = hasattr(backend, "launch_bundle") and hasattr(backend, "wait_bundle")
     # queue: refused since room last freed up; fresh: arrived, not yet tried.
     # A refused submission changes nothing and room frees only when results
     # are read, so queued requests are retried only after that.
@@ -113,11 +125,13 @@ def serve(requests, arrivals, backend, clock=time.perf_counter, keep_results=Fal
     freed = False
     active = {}
     t0 = clock()
-    while pending or queue or fresh or active:
+
+    def admit():
+        nonlocal queue, fresh, freed
         now = clock() - t0
         while pending and pending[0][0] <= now:
             fresh.append(pending.popleft()[1])
-        # admission in arrival order; later requests may pass one that does not fit yet
+        # arrival order; later requests may pass one that does not fit yet
         candidates = (queue + fresh) if freed else fresh
         still = deque()
         for req in candidates:
@@ -130,8 +144,18 @@ def serve(requests, arrivals, backend, clock=time.perf_counter, keep_results=Fal
         queue = still if freed else queue + still
         fresh = deque()
         freed = False
-        if active:
-            backend.run_bundle()
+
+    while pending or queue or fresh or active:
+        running = bool(active)
+        if running and overlap:
+            backend.launch_bundle()  # the bundle advances what was resident before this iteration's admissions
+            admit()
+            backend.wait_bundle()
+        else:
+            admit()
+            if running:
+                backend.run_bundle()
+        if running:
             finished = [t for t in active if backend.done(t)]
             for t in finished:
                 req = active.pop(t)
@@ -142,11 +166,13 @@ def serve(requests, arrivals, backend, clock=time.perf_counter, keep_results=Fal
                 if keep_results:
                     rec.result = res
             freed = freed or bool(finished)
+        elif active:
+            continue  # first admissions: step them next iteration
         elif pending and not queue:
             wait = pending[0][0] - (clock() - t0)
             if wait > 0:
                 time.sleep(min(wait, idle_sleep) if idle_sleep else 0)
-        elif queue and not active:
+        elif queue:
             raise RuntimeError(f"request {queue[0].rid} can never be admitted (larger than the pool budget?)")
     return [records[r.rid] for r in requests]
 

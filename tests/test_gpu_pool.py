@@ -152,3 +152,42 @@ def test_serving_loop_with_poisson_arrivals():
                 assert np.array_equal(a, b)
     s = serving.summarize(recs)
     assert s["ok"] >= 1 and s["ok"] + s["nonfinite"] == len(reqs) and s["p99_ms"] > 0
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_admission_during_a_running_bundle(prec):
+    """Requests admitted while a bundle is on the GPU (pool.run without a
+    sync, then submit) are initialised on the admission stream and join at
+    the next bundle; every result still equals the instance run alone,
+    bitwise, including the instances the running bundle was advancing and
+    one that reuses the memory and slot of a retired instance."""
+    from paper_1608_06345_gb300 import lbm
+    reqs = tube_requests(6, seed=11)
+    pool = lbm.Pool(0, prec, budget_bytes=256 << 20, max_instances=3, bundle_steps=8)
+    tickets = {}
+    waiting = list(reqs)
+    for r in waiting[:2]:
+        tickets[pool.submit(r.gamma, r.tau_f, r.tau_g, r.shape, r.bc, r.fields, r.steps, rho0=r.rho0, T0=r.T0)] = r
+    waiting = waiting[2:]
+    checked = 0
+    while tickets or waiting:
+        pool.run(1)  # in flight while the next admissions are made
+        while waiting:
+            r = waiting[0]
+            t = pool.submit(r.gamma, r.tau_f, r.tau_g, r.shape, r.bc, r.fields, r.steps, rho0=r.rho0, T0=r.T0)
+            if t is None:
+                break
+            tickets[t] = r
+            waiting.pop(0)
+        pool.sync()
+        for t in [t for t in tickets if pool.poll(t)[0]]:
+            r = tickets.pop(t)
+            rc, got = pool.result(t, r.cells)
+            status, ref = solo_status(r, prec)  # this stream holds a tube that diverges in the scheme itself
+            assert status == ("ok" if rc == lbm.LBM_OK else "nonfinite"), r.rid
+            if status == "ok":
+                for a, b in zip(got, ref):
+                    assert np.array_equal(a, b), (r.rid, np.max(np.abs(a - b)))
+            checked += 1
+    assert checked == len(reqs)
+    pool.close()

@@ -127,3 +127,47 @@ def test_refused_requests_wait_for_freed_room():
     assert pool.peak <= 500
     # every attempt is either an admission or a refusal in a fresh generation
     assert pool.attempts <= len(reqs) * (pool.generation + 1)
+
+
+class OverlapPool(FakePool):
+    """FakePool whose bundles are launched and waited for separately; a
+    bundle advances only the requests resident when it was launched, as the
+    GPU pool does with admissions that overlap a running bundle."""
+
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self.in_flight = None
+        self.launches = 0
+        self.advanced = {}
+
+    def launch_bundle(self):
+        assert self.in_flight is None
+        self.in_flight = list(self.res)
+        self.launches += 1
+
+    def wait_bundle(self):
+        for t in self.in_flight:
+            if t in self.res:
+                v = self.res[t]
+                if v[1] < v[0].steps:
+                    self.advanced[t] = self.advanced.get(t, 0) + 1
+                v[1] = min(v[0].steps, v[1] + self.bundle)
+        self.in_flight = None
+
+    def result(self, t, req):
+        # a bundle launched before the admission must not have advanced it
+        assert self.advanced.get(t, 0) == -(-req.steps // self.bundle), (req.rid, self.advanced.get(t))
+        return super().result(t, req)
+
+    def run_bundle(self):
+        raise AssertionError("the loop should launch and wait instead")
+
+
+def test_admissions_overlap_the_running_bundle():
+    reqs = make_requests(50, seed=9)
+    arr = np.sort(np.random.default_rng(3).uniform(0, 0.005, len(reqs)))
+    pool = OverlapPool(budget_cells=700, bundle_steps=40)
+    recs = serving.serve(reqs, arr, pool, idle_sleep=0)
+    assert all(r.status == "ok" for r in recs)
+    assert pool.peak <= 700
+    assert pool.launches >= max(-(-r.steps // 40) for r in reqs)
