@@ -104,14 +104,17 @@ int lbm_init(lbm_handle h, const double* rho, const double* u, const double* T);
 /* As lbm_init with device arrays; asynchronous on the instance's stream. */
 int lbm_init_device(lbm_handle h, const double* rho, const double* u, const double* T);
 
-/* Advance n >= 0 time steps (pull-stream + BGK collide of g and h per step).
- * Asynchronous on the instance's stream.  Runs of at least twice the graph
+/* Advance n >= 0 time steps (pull-stream + BGK collide of g and h per step:
+ * Eq. (16)/(17) with the convection done by exact streaming, xi_i dt = c_i dx,
+ * which the time mapping of Sec. V implies).  Asynchronous on the instance's
+ * stream.  Runs of at least twice the graph
  * length (lbm_set_graph_steps, default 64) replay a captured CUDA graph of
  * that many steps instead of launching each step; the arithmetic is the same. */
 int lbm_step(lbm_handle h, long n);
 
 /* Steps per CUDA graph replay of lbm_step (even, 0..4096); 0 launches every
- * step separately (the plain one-launch-per-step path). */
+ * step separately (the plain one-launch-per-step path).  Execution control
+ * with no counterpart in the paper. */
 int lbm_set_graph_steps(lbm_handle h, int steps);
 
 /* Advance n >= 0 time steps of the finite-difference variant of Sec. III:
@@ -190,7 +193,8 @@ int lbm_lattice_table(int lattice, int* q, int* c, double* w, double* r);
 int lbm_conserved_noalloc(int lattice, int prec, double gamma, double rho0, double T0, const void* state,
                           long long ncells, long long plane_stride, void* stream, double* out);
 
-/* Launch shapes of the step kernel.  Each (lattice, precision) has a small
+/* Launch shapes of the step kernel (execution control with no counterpart in
+ * the paper; every shape computes the same step).  Each (lattice, precision) has a small
  * table of compiled candidates (how the pulled values are staged --
  * registers, shared memory by cp.async, g in registers and h in shared
  * memory (stages 0-3), the velocities of each cell split over 4 warps
@@ -217,10 +221,12 @@ int lbm_autotune(lbm_handle h, int reps, int* best_index, double* best_us);
  * precision (shock tubes and periodic boxes of different sizes, gamma, tau,
  * step counts) resident in one device arena and advanced together by one
  * batched launch per time step.  Instances are admitted against the memory
- * budget as they arrive and retired when their results are read, between
- * step bundles; each instance computes exactly what it would alone.
- * Typical loop: submit arrivals (LBM_EBUSY = wait) -> lbm_pool_run(1) ->
- * lbm_pool_poll each ticket -> lbm_pool_result for finished ones.
+ * budget as they arrive and retired when their results are read; each
+ * instance computes exactly what it would alone (bitwise).  Serving machinery
+ * with no counterpart in the paper; the step itself is lbm_step's.
+ * Typical loop: lbm_pool_run(1) -> submit arrivals while the bundle runs
+ * (LBM_EBUSY = wait for results) -> lbm_pool_sync -> lbm_pool_poll each
+ * ticket -> lbm_pool_result for finished ones.
  * ------------------------------------------------------------------------ */
 typedef struct lbm_pool* lbm_pool_handle;
 
