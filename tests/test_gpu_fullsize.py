@@ -1,7 +1,7 @@
 """Parity at full size, in the launch configuration bench.py times (autotuned
-shape): 4096^2 D2Q37 (FP32 and FP16 storage) and 256^3 D3Q107 FP32, seeded
-Fourier fields; and 272^3 D3Q107 FP32, whose element indices exceed 2^32
-(the 64-bit addressing path).
+shape): 4096^2 D2Q37 (FP32, FP16 and BF16 storage) and 256^3 D3Q107 (FP32 at
+gamma 1.4 and 1.3, FP16 storage), seeded Fourier fields; and 272^3 D3Q107
+FP32, whose element indices exceed 2^32 (the 64-bit addressing path).
 
 The oracle cannot step these grids in a test, so it checks sampled cells one
 by one: after k steps a cell depends only on the cells within 3k of it, so
@@ -118,4 +118,36 @@ def test_d3q107_fp32_272_indexes_in_64_bits():
     s.sync()
     assert abs(c1[0] - c0[0]) / c0[0] <= 4 * 10 * 2.0 ** -24
     assert abs(c1[-1] - c0[-1]) / c0[-1] <= 4 * 10 * 2.0 ** -24
+    s.close()
+
+
+def test_d3q107_fp32_256_gamma_1_3():
+    """The second gamma of the 256^3 workload (delta = 11/3, non-integer)."""
+    shape = (256, 256, 256)
+    fields = li.fourier_fields(shape, seed_u=3, seed_rho=4, seed_T=5)
+    s = sampled_parity(1, shape, fields, 1, 1.3, 0.6, 0.6, TOL["f32"], seed=2)
+    c0 = s.conserved()
+    s.step(20)
+    c1 = s.conserved()
+    s.sync()
+    assert abs(c1[0] - c0[0]) / c0[0] <= 4 * 23 * 2.0 ** -24
+    assert abs(c1[-1] - c0[-1]) / c0[-1] <= 4 * 23 * 2.0 ** -24
+    s.close()
+
+
+def test_d2q37_bf16_storage_4096():
+    shape = (4096, 4096)
+    fields = li.fourier_fields(shape, seed_u=1, seed_rho=2)
+    s = sampled_parity(0, shape, fields, 3, 1.4, 0.55, 0.7, 1e-2, seed=3)
+    s.step(200 - K)
+    s.sync()
+    s.close()
+
+
+def test_d3q107_fp16_storage_256():
+    shape = (256, 256, 256)
+    fields = li.fourier_fields(shape, seed_u=3, seed_rho=4, seed_T=5)
+    s = sampled_parity(1, shape, fields, 2, 1.4, 0.6, 0.6, 1e-3, seed=4)
+    s.step(100 - K)
+    s.sync()
     s.close()
