@@ -78,6 +78,11 @@ def test_library_table_isotropy(lib, lat, D, Q):
     (dict(prec=9), "precision"),
     (dict(bc=(5, 0, 0)), "boundary"),
     (dict(lattice=7), "lattice"),
+    (dict(shape=(65536, 32768)), "2^31"),
+    (dict(shape=(4, 70000)), "65535"),
+    (dict(gamma=float("nan")), "gamma"),
+    (dict(tau_f=float("nan")), "tau"),
+    (dict(lattice=1, shape=(8, 8, 0)), "dimensions"),
 ])
 def test_create_rejects_invalid_arguments(lib, kwargs, msg):
     p = dict(lattice=0, gamma=1.4, tau_f=0.6, tau_g=0.6, shape=(8, 4), prec=lbm.LBM_F32, bc=(0, 0, 0))
