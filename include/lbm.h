@@ -194,12 +194,13 @@ int lbm_conserved_noalloc(int lattice, int prec, double gamma, double rho0, doub
                           long long ncells, long long plane_stride, void* stream, double* out);
 
 /* Launch shapes of the step kernel (execution control with no counterpart in
- * the paper; every shape computes the same step, the stage-4 shapes up to the
- * summation order of the moments).  Each (lattice, precision) has a small
+ * the paper; every shape computes the same step, the stage-4 and stage-7
+ * shapes up to the summation order of the moments).  Each (lattice, precision) has a small
  * table of compiled candidates (how the pulled values are staged --
  * registers, shared memory by cp.async, g in registers and h in shared
  * memory (stages 0-3), the velocities of each cell split over 4 warps
- * (stage 4), or, for 16-bit storage, the (g, h) pairs held packed in
+ * (stage 4; stage 7 with the per-cell equilibrium coefficients formed once
+ * and shared), or, for 16-bit storage, the (g, h) pairs held packed in
  * registers (stage 6) -- and the cells per thread block); index 0 is the
  * default.
  * lbm_shape_info describes candidate `index` (LBM_EINVAL past the end). */

@@ -497,14 +497,15 @@ __device__ __forceinline__ void moments_finish(const C (&acc)[5], const Args<C>&
 // FD: the finite-difference variant of Sec. III, which relaxes the cell's own
 // values and subtracts the convection term conv(I) = {c_g, c_h} (in the
 // stored scale) from the relaxed values.
-// relax_store: the relaxation and store of the velocities [IB, IE) of a cell
-// whose moments (drho, u, dT) are known; cell is the element index within a
-// plane (32 bits: below 2^32 cells per instance)
+// relax_store_k: the relaxation and store of the velocities [IB, IE) of a
+// cell whose equilibrium coefficients k (formed from its moments by
+// eq_coeffs) are known; cell is the element index within a plane (32 bits:
+// below 2^32 cells per instance)
 template <int LAT, class S, class C, bool IDX32, bool FD, int IB = 0, int IE = Lat<LAT>::Q, class GetG, class GetH,
           class Conv>
-__device__ __forceinline__ void relax_store(GetG&& getg, GetH&& geth, Conv&& conv, const Args<C>& a, C drho,
-                                            const C (&u)[3], C dT, S* __restrict__ dst, long long ps,
-                                            unsigned cell) {
+__device__ __forceinline__ void relax_store_k(GetG&& getg, GetH&& geth, Conv&& conv, const Args<C>& a,
+                                              const EqCoef<LAT, C>& k, S* __restrict__ dst, long long ps,
+                                              unsigned cell) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
   constexpr bool SCALED = IsS16<S>::value;
@@ -517,11 +518,9 @@ __device__ __forceinline__ void relax_store(GetG&& getg, GetH&& geth, Conv&& con
     if constexpr (IDX32) dst[(unsigned)plane * (unsigned)ps + cell] = v;
     else *reinterpret_cast<S*>(db + (size_t)plane * pb) = v;
   };
-  EqCoef<LAT, C> k;
-  eq_coeffs<LAT, C>(drho, u, dT, a, k);
   const C hA = a.omega_g * a.half_delta * k.T;
   const C om1 = C(1) - a.omega_g;
-  const C hbs = a.omega_g * a.half_delta * dT;
+  const C hbs = a.omega_g * a.half_delta * k.dT;
   C ig = C(1), hAs = hA, hbg = C(0);  // per-group: 1/gref, hA/hs, hbs gref/hs (16-bit)
   eq_emit<LAT, C, IB, IE>(k, a, [&](auto I, C dF) {
     constexpr int i = decltype(I)::value;
@@ -557,6 +556,17 @@ __device__ __forceinline__ void relax_store(GetG&& getg, GetH&& geth, Conv&& con
       st(Q + i, static_cast<S>(hn));
     }
   });
+}
+
+// relax_store_k with the equilibrium coefficients formed from the moments
+template <int LAT, class S, class C, bool IDX32, bool FD, int IB = 0, int IE = Lat<LAT>::Q, class GetG, class GetH,
+          class Conv>
+__device__ __forceinline__ void relax_store(GetG&& getg, GetH&& geth, Conv&& conv, const Args<C>& a, C drho,
+                                            const C (&u)[3], C dT, S* __restrict__ dst, long long ps,
+                                            unsigned cell) {
+  EqCoef<LAT, C> k;
+  eq_coeffs<LAT, C>(drho, u, dT, a, k);
+  relax_store_k<LAT, S, C, IDX32, FD, IB, IE>(getg, geth, conv, a, k, dst, ps, cell);
 }
 
 template <int LAT, class S, class C, bool IDX32, bool FD, class GetG, class GetH, class Conv>
@@ -784,7 +794,10 @@ struct Split {
   }
 };
 
-template <int LAT, class S, class C, int P, int MINB>
+// SHARE: warp 0 alone finishes the moments and forms the equilibrium
+// coefficients, which the other warps read from shared memory after a second
+// barrier (less arithmetic per cell; worth it where the FP64 pipe is the bound)
+template <int LAT, class S, class C, int P, int MINB, bool SHARE = false>
 __global__ void __launch_bounds__(32 * P, MINB) k_step_split(const S* __restrict__ src, S* __restrict__ dst,
                                                             const Args<C> a) {
   using L = Lat<LAT>;
@@ -839,25 +852,40 @@ __global__ void __launch_bounds__(32 * P, MINB) k_step_split(const S* __restrict
     }
   });
   __syncthreads();
-  C acc[5];
+  auto finish = [&](EqCoef<LAT, C>& k) {  // sum the parts in a fixed order, then the cell's coefficients
+    C acc[5];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    C v = red[0][k][lane];
+    for (int q = 0; q < 5; ++q) {
+      C v = red[0][q][lane];
 #pragma unroll
-    for (int p = 1; p < P; ++p) v += red[p][k][lane];
-    acc[k] = v;
+      for (int p = 1; p < P; ++p) v += red[p][q][lane];
+      acc[q] = v;
+    }
+    C drho, u[3], dT;
+    moments_finish<LAT, C>(acc, a, drho, u, dT);
+    if (w == 0 && active && !(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+    eq_coeffs<LAT, C>(drho, u, dT, a, k);
+  };
+  EqCoef<LAT, C> k;
+  if constexpr (SHARE) {
+    __shared__ EqCoef<LAT, C> shk[32];
+    if (w == 0) {
+      finish(k);
+      shk[lane] = k;
+    }
+    __syncthreads();
+    if (w != 0) k = shk[lane];
+  } else {
+    finish(k);
   }
-  C drho, u[3], dT;
-  moments_finish<LAT, C>(acc, a, drho, u, dT);
   if (!active) return;
-  if (w == 0 && !(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
   // phase 2: relax and store this warp's velocities
   static_for<P>([&](auto W) {
     constexpr int IB = SP::begin(decltype(W)::value), IE = SP::end(decltype(W)::value);
     if (w == decltype(W)::value)
-      relax_store<LAT, S, C, false, false, IB, IE>(
+      relax_store_k<LAT, S, C, false, false, IB, IE>(
           [&](auto I) { return g[decltype(I)::value - IB]; }, [&](auto I) { return h[decltype(I)::value - IB]; },
-          [](auto) { return ConvGH<C>{C(0), C(0)}; }, a, drho, u, dT, dst, ps, cell);
+          [](auto) { return ConvGH<C>{C(0), C(0)}; }, a, k, dst, ps, cell);
   });
 }
 

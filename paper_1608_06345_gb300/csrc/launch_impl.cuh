@@ -62,12 +62,12 @@ cudaError_t launch_step_t(const Instance* inst, const void* src, void* dst, cons
 }
 
 // the velocity-split step: 32 cells per block, P warps (static shared memory only)
-template <int LAT, class S, class C, int P, int MINB>
+template <int LAT, class S, class C, int P, int MINB, bool SHARE = false>
 cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, const Args<C>& a,
                               bool configure_only = false) {
   if (configure_only) return cudaSuccess;
   const dim3 grid((unsigned)((inst->n[0] + 31) / 32), (unsigned)inst->n[1], (unsigned)inst->n[2]);
-  k_step_split<LAT, S, C, P, MINB><<<grid, dim3(32, P), 0, inst->stream>>>(static_cast<const S*>(src),
+  k_step_split<LAT, S, C, P, MINB, SHARE><<<grid, dim3(32, P), 0, inst->stream>>>(static_cast<const S*>(src),
                                                                            static_cast<S*>(dst), a);
   return cudaGetLastError();
 }
@@ -77,24 +77,25 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
 // resident blocks per SM requested from the compiler, which caps registers):
 //   D2Q37 FP32:        (0,128,4) (0,256,2) (0,64,8) (0,128,1)
 //   D2Q37 16-bit:      (6,128,8) (6,128,7) (6,128,6) (6,256,3) (0,128,4) (0,64,8)
-//   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)  (4,32,4)
+//   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)  (4,32,4)  (7,32,4)
 //   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)
-//   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)
+//   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)  (7,32,3)
 //   D3Q107 16-bit:     (6,64,6)  (2,64,8)  (2,64,1)  (4,32,6)
-// Stage 4 is the velocity-split step: 4 warps per block of 32 cells.  Its
+// Stage 4 is the velocity-split step: 4 warps per block of 32 cells; stage 7
+// the same with the per-cell coefficients formed once by warp 0 and shared.  Its
 // moments are summed in another order, so its results differ from the
 // other shapes' by rounding; the defaults (index 0) are the shapes the
 // batched pool uses, whose results are bitwise those of a lone instance.
 template <int LAT, class S>
 struct StepShapes {
   static constexpr int count =
-      (LAT == 0) ? (sizeof(S) == 8 ? 4 : (sizeof(S) == 2 ? 6 : 4)) : (sizeof(S) == 8 ? 3 : 4);
+      (LAT == 0) ? (sizeof(S) == 8 ? 5 : (sizeof(S) == 2 ? 6 : 4)) : (sizeof(S) == 8 ? 4 : 4);
   static void get(int k, int* stage, int* bx, int* minb) {
     static const int s2[4][3] = {{0, 128, 4}, {0, 256, 2}, {0, 64, 8}, {0, 128, 1}};
     static const int s2h[6][3] = {{6, 128, 8}, {6, 128, 7}, {6, 128, 6}, {6, 256, 3}, {0, 128, 4}, {0, 64, 8}};
-    static const int s2d[4][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}, {4, 32, 4}};
+    static const int s2d[5][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}, {4, 32, 4}, {7, 32, 4}};
     static const int s3f[4][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}};
-    static const int s3d[3][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}};
+    static const int s3d[4][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}, {7, 32, 3}};
     static const int s3h[4][3] = {{6, 64, 6}, {2, 64, 8}, {2, 64, 1}, {4, 32, 6}};
     const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : (sizeof(S) == 2 ? s2h : s2))
                                   : (sizeof(S) == 4 ? s3f : (sizeof(S) == 8 ? s3d : s3h));
@@ -122,6 +123,7 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
       case 1: return launch_step_t<LAT, S, C, 0, 256>(inst, src, dst, a, configure_only);
       case 2: return launch_step_t<LAT, S, C, 0, 64>(inst, src, dst, a, configure_only);
       case 3: return launch_step_split<LAT, S, C, 4, 4>(inst, src, dst, a, configure_only);
+      case 4: return launch_step_split<LAT, S, C, 4, 4, true>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 0, 128>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (LAT == 0 && sizeof(S) == 2) {
@@ -151,6 +153,7 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
     switch (k) {
       case 1: return launch_step_split<LAT, S, C, 4, 3>(inst, src, dst, a, configure_only);
       case 2: return launch_step_split<LAT, S, C, 4, 2>(inst, src, dst, a, configure_only);
+      case 3: return launch_step_split<LAT, S, C, 4, 3, true>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
     }
   } else {
