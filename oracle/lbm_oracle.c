@@ -39,6 +39,56 @@
 #include <omp.h>
 #endif
 
+/* Rounding variants.  ORA_VARIANT changes how the arithmetic below is
+ * rounded, never what it computes.  The tests build the variants as second
+ * checkers: how far a variant's result lies from the oracle's measures how
+ * far two correct FP64 evaluations of the same scheme drift apart on a given
+ * flow.  The bits of ORA_VARIANT:
+ *   0  (default build) the oracle;
+ *   1  every sum over the velocities runs from the last velocity to the
+ *      first, and the terms of the equilibrium are added from the highest
+ *      order down;
+ *   2  every product-plus-sum a*b + c of the moments, the equilibrium's
+ *      scalar products and the relaxation is rounded once (C99 fma);
+ *   4  the relaxation q - (q - Q_eq)/tau is evaluated as
+ *      (1 - 1/tau) q + (1/tau) Q_eq;
+ *   8  the populations are held as deviations from the equilibrium of a
+ *      reference state (rho_r, u = 0, T_r) set by ora_set_reference:
+ *      dg_i = g_i - G_i, dh_i = h_i - (delta/2) T_r G_i with
+ *      G_i = F_i(rho_r, 0, T_r).  The pull moves deviations, the moments add
+ *      the sums of the deviations to the reference totals (rho_r for the
+ *      mass, rho_r (D + delta) T_r / 2 for the energy: Eq. (14)/(15) of the
+ *      reference equilibrium), and the relaxation updates the deviations
+ *      towards F_i - G_i.  An exact change of variables;
+ *  16  the arithmetic and the stored populations are FP32 (type real; the
+ *      build adds -fsingle-precision-constant so that literals stay FP32);
+ *      the velocity table is still solved in FP64 and rounded, and the
+ *      grid totals of ora_conserved are still summed in FP64.
+ * The default build (0) evaluates every expression exactly as written, in
+ * FP64. */
+#ifndef ORA_VARIANT
+#define ORA_VARIANT 0
+#endif
+#define ORA_REV ((ORA_VARIANT) & 1)
+#define ORA_FMA ((ORA_VARIANT) & 2)
+#define ORA_RELAX2 ((ORA_VARIANT) & 4)
+#define ORA_DEV ((ORA_VARIANT) & 8)
+#define ORA_F32 ((ORA_VARIANT) & 16)
+#if ORA_F32
+typedef float real;
+#define FMA_ fmaf
+#else
+typedef double real;
+#define FMA_ fma
+#endif
+#if ORA_FMA
+#define MADD(a, b, c) FMA_((a), (b), (c))
+#else
+#define MADD(a, b, c) ((a) * (b) + (c))
+#endif
+/* k-th velocity of a sum over Q velocities */
+#define VEL(k, Q) (ORA_REV ? (Q) - 1 - (k) : (k))
+
 #define ORA_D2Q37 0
 #define ORA_D3Q107 1
 #define ORA_PERIODIC 0
@@ -241,48 +291,55 @@ static int build_lattice(int lattice, ora_lattice_t* L) {
  * These are the contractions of the Maxwellian's Hermite coefficients
  * a(2) = uu + t I, a(3) = uuu + t sym(uI), a(4) = uuuu + t sym(uuI)
  * + t^2 sym(II) with the tensor Hermite polynomials. */
-static void equilibrium(const ora_lattice_t* L, double rho, const double* u,
-                        double T, double* F) {
+static void equilibrium(const ora_lattice_t* L, real rho, const real* u,
+                        real T, real* F) {
   const int D = L->D;
-  double u2 = 0.0;
+  real u2 = 0.0;
   for (int a = 0; a < D; ++a) u2 += u[a] * u[a];
-  const double t = T - 1.0;
+  const real t = T - 1.0;
   for (int i = 0; i < L->Q; ++i) {
-    double s = 0.0, x2 = 0.0;
+    real s = 0.0, x2 = 0.0;
     for (int a = 0; a < D; ++a) {
-      double xi = L->r * L->c[i][a];
-      s += xi * u[a];
-      x2 += xi * xi;
+      real xi = (real)L->r * L->c[i][a];
+      s = MADD(xi, u[a], s);
+      x2 = MADD(xi, xi, x2);
     }
-    double h0 = 1.0;
-    double h1 = s;
-    double h2 = s * s - u2 + t * (x2 - D);
-    double h3 = s * (s * s - 3.0 * u2 + 3.0 * t * (x2 - D - 2.0));
-    double h4 = s * s * s * s - 6.0 * s * s * u2 + 3.0 * u2 * u2 +
-                6.0 * t * (s * s * (x2 - D - 4.0) + (D + 2.0 - x2) * u2) +
-                3.0 * t * t * (x2 * x2 - 2.0 * (D + 2.0) * x2 + D * (D + 2.0));
-    F[i] = L->w[i] * rho * (h0 + h1 + h2 / 2.0 + h3 / 6.0 + h4 / 24.0);
+    real h0 = 1.0;
+    real h1 = s;
+    real h2 = s * s - u2 + t * (x2 - D);
+    real h3 = s * (s * s - 3.0 * u2 + 3.0 * t * (x2 - D - 2.0));
+    real h4 = s * s * s * s - 6.0 * s * s * u2 + 3.0 * u2 * u2 +
+              6.0 * t * (s * s * (x2 - D - 4.0) + (D + 2.0 - x2) * u2) +
+              3.0 * t * t * (x2 * x2 - 2.0 * (D + 2.0) * x2 + D * (D + 2.0));
+#if ORA_REV
+    F[i] = (real)L->w[i] * rho * (h4 / 24.0 + h3 / 6.0 + h2 / 2.0 + h1 + h0);
+#else
+    F[i] = (real)L->w[i] * rho * (h0 + h1 + h2 / 2.0 + h3 / 6.0 + h4 / 24.0);
+#endif
   }
 }
 
 /* Moments of one cell, Eq. (14a-c) and Eq. (15a,b):
  *   rho = sum g_i, rho u = sum xi_i g_i, rho E = sum xi_i^2 g_i / 2 + sum h_i,
- *   E = u^2/2 + (D + delta)/2 T  =>  T = 2 (E - u^2/2) / (D + delta). */
-static void cell_moments(const ora_lattice_t* L, double delta, const double* g,
-                         const double* h, double* rho, double* u, double* T) {
+ *   E = u^2/2 + (D + delta)/2 T  =>  T = 2 (E - u^2/2) / (D + delta).
+ * m0, e0 are added to the mass and energy sums: 0 in the oracle, whose
+ * populations are stored whole; the reference totals in variant 8. */
+static void cell_moments(const ora_lattice_t* L, real delta, real m0, real e0,
+                         const real* g, const real* h, real* rho, real* u, real* T) {
   const int D = L->D;
-  double r0 = 0.0, j[3] = {0.0, 0.0, 0.0}, e = 0.0;
-  for (int i = 0; i < L->Q; ++i) {
-    double x2 = 0.0;
+  real r0 = m0, j[3] = {0.0, 0.0, 0.0}, e = e0;
+  for (int k = 0; k < L->Q; ++k) {
+    const int i = VEL(k, L->Q);
+    real x2 = 0.0;
     for (int a = 0; a < D; ++a) {
-      double xi = L->r * L->c[i][a];
-      j[a] += xi * g[i];
-      x2 += xi * xi;
+      real xi = (real)L->r * L->c[i][a];
+      j[a] = MADD(xi, g[i], j[a]);
+      x2 = MADD(xi, xi, x2);
     }
     r0 += g[i];
-    e += 0.5 * x2 * g[i] + h[i];
+    e += MADD(0.5 * x2, g[i], h[i]);
   }
-  double u2 = 0.0;
+  real u2 = 0.0;
   for (int a = 0; a < D; ++a) {
     u[a] = j[a] / r0;
     u2 += u[a] * u[a];
@@ -301,9 +358,14 @@ typedef struct {
   int n[3];        /* nx, ny, nz (nz = 1 in 2D) */
   int bc[3];       /* per axis: periodic or zero-gradient */
   long N;          /* cells */
-  double *g, *h;   /* populations, g[i * N + cell] */
-  double *g2, *h2; /* second buffer */
+  real *g, *h;     /* populations, g[i * N + cell] */
+  real *g2, *h2;   /* second buffer */
+  /* variant 8 only: the reference equilibrium G_i, (delta/2) T_r G_i and its
+   * mass and energy totals; zero in the oracle */
+  real ref_g[107], ref_h[107], ref_m, ref_e;
 } ora_state;
+
+int ora_set_reference(ora_state* s, double rho_r, double T_r);
 
 /* delta from gamma, Eq. (3): gamma = (delta + D + 2) / (delta + D). */
 double ora_delta_from_gamma(int D, double gamma) {
@@ -329,7 +391,10 @@ int ora_feq(int lattice, double rho, const double* u, double T, double* F) {
   ora_lattice_t L;
   int rc = build_lattice(lattice, &L);
   if (rc) return rc;
-  equilibrium(&L, rho, u, T, F);
+  real ur[3] = {0.0, 0.0, 0.0}, Fr[107];
+  for (int a = 0; a < L.D; ++a) ur[a] = (real)u[a];
+  equilibrium(&L, (real)rho, ur, (real)T, Fr);
+  for (int i = 0; i < L.Q; ++i) F[i] = Fr[i];
   return 0;
 }
 
@@ -368,11 +433,14 @@ ora_state* ora_new(int lattice, double gamma, double tau_f, double tau_g,
   s->n[0] = nx; s->n[1] = ny; s->n[2] = nz;
   s->bc[0] = bcx; s->bc[1] = bcy; s->bc[2] = bcz;
   s->N = (long)nx * ny * nz;
-  size_t bytes = sizeof(double) * (size_t)s->L.Q * (size_t)s->N;
-  s->g = (double*)malloc(bytes);
-  s->h = (double*)malloc(bytes);
-  s->g2 = (double*)malloc(bytes);
-  s->h2 = (double*)malloc(bytes);
+#if ORA_DEV
+  ora_set_reference(s, 1.0, 1.0);
+#endif
+  size_t bytes = sizeof(real) * (size_t)s->L.Q * (size_t)s->N;
+  s->g = (real*)malloc(bytes);
+  s->h = (real*)malloc(bytes);
+  s->g2 = (real*)malloc(bytes);
+  s->h2 = (real*)malloc(bytes);
   if (!s->g || !s->h || !s->g2 || !s->h2) { ora_free(s); return NULL; }
   return s;
 }
@@ -384,14 +452,21 @@ double ora_delta(const ora_state* s) { return s->delta; }
 void ora_init(ora_state* s, const double* rho, const double* u, const double* T) {
   const long N = s->N;
   const int Q = s->L.Q, D = s->L.D;
+  const real hd = (real)(0.5 * s->delta);
 #pragma omp parallel for schedule(static)
   for (long cell = 0; cell < N; ++cell) {
-    double F[107], uc[3];
-    for (int a = 0; a < D; ++a) uc[a] = u[a * N + cell];
-    equilibrium(&s->L, rho[cell], uc, T[cell], F);
+    real F[107], uc[3];
+    const real Tc = (real)T[cell];
+    for (int a = 0; a < D; ++a) uc[a] = (real)u[a * N + cell];
+    equilibrium(&s->L, (real)rho[cell], uc, Tc, F);
     for (int i = 0; i < Q; ++i) {
+#if ORA_DEV
+      s->g[i * N + cell] = F[i] - s->ref_g[i];
+      s->h[i * N + cell] = hd * Tc * F[i] - s->ref_h[i];
+#else
       s->g[i * N + cell] = F[i];
-      s->h[i * N + cell] = 0.5 * s->delta * T[cell] * F[i];
+      s->h[i * N + cell] = hd * Tc * F[i];
+#endif
     }
   }
 }
@@ -420,11 +495,12 @@ static void step_once(ora_state* s) {
   const long N = s->N;
   const int Q = s->L.Q, D = s->L.D;
   const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
-  const double wf = 1.0 / s->tau_f, wg = 1.0 / s->tau_g;
+  const real wf = (real)(1.0 / s->tau_f), wg = (real)(1.0 / s->tau_g);
+  const real hd = (real)(0.5 * s->delta);
 #pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y) {
-      double gt[107], ht[107], F[107], u[3], rho, T;
+      real gt[107], ht[107], F[107], u[3], rho, T;
       for (int x = 0; x < nx; ++x) {
         long cell = x + (long)nx * (y + (long)ny * z);
         for (int i = 0; i < Q; ++i) {
@@ -435,17 +511,26 @@ static void step_once(ora_state* s) {
           gt[i] = s->g[i * N + src];
           ht[i] = s->h[i * N + src];
         }
-        cell_moments(&s->L, s->delta, gt, ht, &rho, u, &T);
+        cell_moments(&s->L, (real)s->delta, s->ref_m, s->ref_e, gt, ht, &rho, u, &T);
         equilibrium(&s->L, rho, u, T, F);
         for (int i = 0; i < Q; ++i) {
-          double Fh = 0.5 * s->delta * T * F[i];
-          s->g2[i * N + cell] = gt[i] - wf * (gt[i] - F[i]);
-          s->h2[i * N + cell] = ht[i] - wg * (ht[i] - Fh);
+          real Fh = hd * T * F[i];
+#if ORA_DEV
+          Fh -= s->ref_h[i];
+          F[i] -= s->ref_g[i];
+#endif
+#if ORA_RELAX2
+          s->g2[i * N + cell] = MADD(1.0 - wf, gt[i], wf * F[i]);
+          s->h2[i * N + cell] = MADD(1.0 - wg, ht[i], wg * Fh);
+#else
+          s->g2[i * N + cell] = MADD(-wf, gt[i] - F[i], gt[i]);
+          s->h2[i * N + cell] = MADD(-wg, ht[i] - Fh, ht[i]);
+#endif
         }
       }
     }
   (void)D;
-  double* t;
+  real* t;
   t = s->g; s->g = s->g2; s->g2 = t;
   t = s->h; s->h = s->h2; s->h2 = t;
 }
@@ -466,9 +551,9 @@ void ora_step(ora_state* s, long nsteps) {
  *   sgn < 0:  [-q(p+2) + 6 q(p+1) - 3 q(p) - 2 q(p-1)] / 6
  * Neighbours outside the grid follow the axis' boundary rule (periodic wrap
  * or the edge cell).  `at(k)` reads q at axis position k. */
-static double upwind3(int p, int sgn, int n, int bc, const double* plane, long stride, long base) {
+static real upwind3(int p, int sgn, int n, int bc, const real* plane, long stride, long base) {
 #define Q_AT(k) plane[base + (long)pull_index((p), -(k), (n), (bc)) * stride]
-  double d;
+  real d;
   if (sgn > 0)
     d = (Q_AT(-2) - 6.0 * Q_AT(-1) + 3.0 * Q_AT(0) + 2.0 * Q_AT(1)) / 6.0;
   else
@@ -487,11 +572,12 @@ static void step_fd_once(ora_state* s, double lambda) {
   const int Q = s->L.Q, D = s->L.D;
   const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
   const long stride[3] = {1, nx, (long)nx * ny};
-  const double wf = 1.0 / s->tau_f, wg = 1.0 / s->tau_g;
+  const real wf = (real)(1.0 / s->tau_f), wg = (real)(1.0 / s->tau_g);
+  const real hd = (real)(0.5 * s->delta), lam = (real)lambda;
 #pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y) {
-      double gc[107], hc[107], F[107], u[3], rho, T;
+      real gc[107], hc[107], F[107], u[3], rho, T;
       for (int x = 0; x < nx; ++x) {
         const long cell = x + (long)nx * (y + (long)ny * z);
         const int pos[3] = {x, y, z};
@@ -500,25 +586,30 @@ static void step_fd_once(ora_state* s, double lambda) {
           gc[i] = s->g[i * N + cell];
           hc[i] = s->h[i * N + cell];
         }
-        cell_moments(&s->L, s->delta, gc, hc, &rho, u, &T);
+        cell_moments(&s->L, (real)s->delta, s->ref_m, s->ref_e, gc, hc, &rho, u, &T);
         equilibrium(&s->L, rho, u, T, F);
         for (int i = 0; i < Q; ++i) {
-          double cg = 0.0, ch = 0.0;
+          real cg = 0.0, ch = 0.0;
           for (int a = 0; a < D; ++a) {
             const int c = s->L.c[i][a];
             if (c == 0) continue;
-            const double xi = s->L.r * c;
+            const real xi = (real)s->L.r * c;
             const long base = cell - (long)pos[a] * stride[a];
             cg += xi * upwind3(pos[a], c, nn[a], s->bc[a], s->g + i * N, stride[a], base);
             ch += xi * upwind3(pos[a], c, nn[a], s->bc[a], s->h + i * N, stride[a], base);
           }
-          const double Fh = 0.5 * s->delta * T * F[i];
-          s->g2[i * N + cell] = gc[i] - lambda * cg - wf * (gc[i] - F[i]);
-          s->h2[i * N + cell] = hc[i] - lambda * ch - wg * (hc[i] - Fh);
+#if ORA_DEV
+          const real Fh = hd * T * F[i] - s->ref_h[i];
+          F[i] -= s->ref_g[i];
+#else
+          const real Fh = hd * T * F[i];
+#endif
+          s->g2[i * N + cell] = gc[i] - lam * cg - wf * (gc[i] - F[i]);
+          s->h2[i * N + cell] = hc[i] - lam * ch - wg * (hc[i] - Fh);
         }
       }
     }
-  double* t;
+  real* t;
   t = s->g; s->g = s->g2; s->g2 = t;
   t = s->h; s->h = s->h2; s->h2 = t;
 }
@@ -533,12 +624,14 @@ void ora_moments(const ora_state* s, double* rho, double* u, double* T) {
   const int Q = s->L.Q, D = s->L.D;
 #pragma omp parallel for schedule(static)
   for (long cell = 0; cell < N; ++cell) {
-    double g[107], h[107], uc[3];
+    real g[107], h[107], uc[3], rc, Tc;
     for (int i = 0; i < Q; ++i) {
       g[i] = s->g[i * N + cell];
       h[i] = s->h[i * N + cell];
     }
-    cell_moments(&s->L, s->delta, g, h, &rho[cell], uc, &T[cell]);
+    cell_moments(&s->L, (real)s->delta, s->ref_m, s->ref_e, g, h, &rc, uc, &Tc);
+    rho[cell] = rc;
+    T[cell] = Tc;
     for (int a = 0; a < D; ++a) u[a * N + cell] = uc[a];
   }
 }
@@ -553,6 +646,10 @@ void ora_conserved(const ora_state* s, double* out) {
   for (long cell = 0; cell < N; ++cell)
     for (int i = 0; i < Q; ++i) {
       double gi = s->g[i * N + cell], hi = s->h[i * N + cell];
+#if ORA_DEV
+      gi += s->ref_g[i];
+      hi += s->ref_h[i];
+#endif
       double x2 = 0.0;
       for (int a = 0; a < D; ++a) {
         double xi = s->L.r * s->L.c[i][a];
@@ -570,13 +667,49 @@ void ora_conserved(const ora_state* s, double* out) {
 /* Direct access to the populations, [i * N + cell], in the oracle's own
  * velocity order (ora_lattice_info). */
 void ora_get_pops(const ora_state* s, double* g, double* h) {
-  size_t bytes = sizeof(double) * (size_t)s->L.Q * (size_t)s->N;
-  memcpy(g, s->g, bytes);
-  memcpy(h, s->h, bytes);
+  const long n = (long)s->L.Q * s->N;
+  for (long k = 0; k < n; ++k) {
+    g[k] = s->g[k];
+    h[k] = s->h[k];
+  }
+#if ORA_DEV
+  for (int i = 0; i < s->L.Q; ++i)
+    for (long cell = 0; cell < s->N; ++cell) {
+      g[i * s->N + cell] += s->ref_g[i];
+      h[i * s->N + cell] += s->ref_h[i];
+    }
+#endif
 }
 
 void ora_set_pops(ora_state* s, const double* g, const double* h) {
-  size_t bytes = sizeof(double) * (size_t)s->L.Q * (size_t)s->N;
-  memcpy(s->g, g, bytes);
-  memcpy(s->h, h, bytes);
+  const long n = (long)s->L.Q * s->N;
+  for (long k = 0; k < n; ++k) {
+    s->g[k] = (real)g[k];
+    s->h[k] = (real)h[k];
+  }
+#if ORA_DEV
+  for (int i = 0; i < s->L.Q; ++i)
+    for (long cell = 0; cell < s->N; ++cell) {
+      s->g[i * s->N + cell] -= s->ref_g[i];
+      s->h[i * s->N + cell] -= s->ref_h[i];
+    }
+#endif
+}
+
+/* Reference state of variant 8 (rho_r, u = 0, T_r); the default is (1, 1).
+ * Call before ora_init.  Returns -1 in builds without variant 8, whose
+ * populations are stored whole. */
+int ora_set_reference(ora_state* s, double rho_r, double T_r) {
+#if ORA_DEV
+  const real zero[3] = {0.0, 0.0, 0.0};
+  const real hd = (real)(0.5 * s->delta);
+  equilibrium(&s->L, (real)rho_r, zero, (real)T_r, s->ref_g);
+  for (int i = 0; i < s->L.Q; ++i) s->ref_h[i] = hd * (real)T_r * s->ref_g[i];
+  s->ref_m = (real)rho_r;
+  s->ref_e = (real)(0.5 * rho_r * (s->L.D + s->delta) * T_r);
+  return 0;
+#else
+  (void)s; (void)rho_r; (void)T_r;
+  return -1;
+#endif
 }

@@ -22,31 +22,52 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lbm_oracle.c")
 LIB = os.path.join(HERE, "_build", "liblbm_oracle.so")
 
+# Rounding variants of the oracle (bits of ORA_VARIANT in lbm_oracle.c):
+# 1 reversed velocity order of every sum, 2 fused multiply-adds, 4 the
+# relaxation as (1 - 1/tau) q + Q_eq/tau, 8 populations held as deviations
+# from a reference equilibrium (Oracle.set_reference), 16 FP32 arithmetic and
+# storage.  They change rounding only; the tests use them as second checkers
+# to measure how far correct evaluations of the scheme in FP64 (or in FP32)
+# land from the oracle on a flow.
+VARIANTS_F64 = (1, 2, 4, 7, 8, 15)
+VARIANTS_F32 = (16, 17, 18, 20, 23, 24, 31)
+VARIANTS = VARIANTS_F64 + VARIANTS_F32
+
 D2Q37 = 0
 D3Q107 = 1
 PERIODIC = 0
 ZERO_GRADIENT = 1
 
-_lib = None
+_libs = {}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP)."""
+def lib_path(variant: int = 0) -> str:
+    return LIB if variant == 0 else os.path.join(HERE, "_build", f"liblbm_oracle_v{variant}.so")
+
+
+def build(force: bool = False, variants=(0,) + VARIANTS) -> str:
+    """Compile the oracle (and its rounding variants) with gcc: FP64, no
+    FMA contraction by the compiler, OpenMP.  Returns the oracle's path."""
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-               "-fopenmp", "-shared", "-fPIC", SRC, "-o", LIB + ".tmp", "-lm"]
-        subprocess.check_call(cmd)
-        os.replace(LIB + ".tmp", LIB)
+    for v in variants:
+        out = lib_path(v)
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                   "-fopenmp", "-shared", "-fPIC", f"-DORA_VARIANT={v}", SRC, "-o", out + ".tmp", "-lm"]
+            if v & 16:  # FP32 variants: unsuffixed literals stay FP32
+                cmd.insert(1, "-fsingle-precision-constant")
+            subprocess.check_call(cmd)
+            os.replace(out + ".tmp", out)
     return LIB
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    build()
-    lib = ctypes.CDLL(LIB)
+def _load(variant: int = 0):
+    if variant in _libs:
+        return _libs[variant]
+    if variant != 0 and variant not in VARIANTS:
+        raise ValueError(f"unknown oracle variant {variant}")
+    build(variants=(variant,))
+    lib = ctypes.CDLL(lib_path(variant))
     dp = ctypes.POINTER(ctypes.c_double)
     ip = ctypes.POINTER(ctypes.c_int)
     lib.ora_new.restype = ctypes.c_void_p
@@ -71,7 +92,9 @@ def _load():
     lib.ora_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, dp]
     lib.ora_set_threads.argtypes = [ctypes.c_int]
     lib.ora_get_threads.restype = ctypes.c_int
-    _lib = lib
+    lib.ora_set_reference.restype = ctypes.c_int
+    lib.ora_set_reference.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+    _libs[variant] = lib
     return lib
 
 
@@ -125,11 +148,12 @@ def get_threads() -> int:
 
 
 class Oracle:
-    """One FP64 solver instance: ``init`` -> ``step(n)`` -> ``moments``."""
+    """One FP64 solver instance: ``init`` -> ``step(n)`` -> ``moments``.
+    ``variant`` selects a rounding variant (VARIANTS) instead of the oracle."""
 
     def __init__(self, lattice: int, gamma: float, tau_f: float, tau_g: float,
-                 shape, bc=(PERIODIC, PERIODIC, PERIODIC)):
-        lib = _load()
+                 shape, bc=(PERIODIC, PERIODIC, PERIODIC), variant: int = 0):
+        lib = _load(variant)
         self.lattice = lattice
         self.D = dim(lattice)
         shape = tuple(int(s) for s in shape)
@@ -155,6 +179,11 @@ class Oracle:
             self.close()
         except Exception:
             pass
+
+    def set_reference(self, rho_r: float, T_r: float):
+        """Reference state of a deviation variant (bit 8); call before init."""
+        if self._lib.ora_set_reference(self._h, float(rho_r), float(T_r)):
+            raise ValueError("this oracle build stores the populations whole")
 
     def init(self, rho, u, T):
         rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)

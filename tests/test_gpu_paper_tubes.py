@@ -10,16 +10,19 @@ the oracle and the exact Riemann solution:
 
 The tubes are uniform across the tube, so the GPU state stays exactly
 uniform in y and z and a 1000 x 1 (x 1) oracle run is the same computation
-per cell.  Parity uses the conditioned tolerance of tests/parity.py; the
-L1 errors against the exact solution must be small (the paper's figure,
-which would give the level, is missing)."""
+per cell.  Parity is held to max(bar, 2 E), E the largest distance of the
+oracle's rounding variants from the oracle on the same case
+(tests/parity.py); where the variants stay within half the bar (the 2D tube
+at gamma 1.4, 1.1 and 5/3) that is the plain 1e-12.  The L1 errors against
+the exact solution must be small (the paper's figure, which would give the
+level, is missing)."""
 import numpy as np
 import pytest
 
 import lbm_inputs as li
 from oracle import oracle as ora
 from oracle import riemann
-from tests.parity import assert_parity, conditioned_tolerance, run_gpu, run_oracle, sensitivity
+from tests.parity import assert_parity, report, run_gpu, run_variants, spread_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -38,8 +41,7 @@ def test_paper_tube_3d_1000x16x16(prec):
     lat, nx, steps, gamma, tau = ora.D3Q107, 1000, 180, 1.4, 2.0 / 3.0
     bc = (ora.ZERO_GRADIENT, ora.PERIODIC, ora.PERIODIC)
     f1 = li.sod_fields(nx, 1, 1, D=3, left=LEFT, right=RIGHT)
-    ref, _ = run_oracle(lat, gamma, tau, tau, (nx, 1, 1), bc, f1, steps)
-    kappa = sensitivity(lat, gamma, tau, tau, (nx, 1, 1), bc, f1, steps, prec, ref=ref)
+    E, _, ref, _ = run_variants(lat, gamma, tau, tau, (nx, 1, 1), bc, f1, steps, prec)
     gpu, _ = run_gpu(1, gamma, tau, tau, (nx, 16, 16), bc, li.sod_fields(nx, 16, 16, D=3, left=LEFT, right=RIGHT),
                      steps, prec)
     # uniform across the tube: every (y, z) row equals row 0 bitwise
@@ -47,7 +49,8 @@ def test_paper_tube_3d_1000x16x16(prec):
         rows = q.reshape(16 * 16, nx)
         assert np.all(rows == rows[0])
     g0 = (gpu[0][:nx], gpu[1][:, :nx], gpu[2][:nx])
-    assert_parity(g0, ref, gamma, conditioned_tolerance(prec, kappa, steps))
+    tol = spread_tolerance(prec, E)
+    report(f"paper tube 3D 1000x16x16 {'FP64' if prec == 0 else 'FP32'}", assert_parity(g0, ref, gamma, tol), E, tol)
     _, _, r = ora.lattice_info(lat)
     e = l1_vs_exact(gpu, nx, gamma, steps, r)
     assert e[0] < 0.03 and e[1] < 0.01 and e[2] < 0.01, e
@@ -58,11 +61,11 @@ def test_paper_tube_2d_gamma_sweep(gamma):
     lat, nx, steps, tau = ora.D2Q37, 1000, 180, 2.0 / 3.0
     bc = (ora.ZERO_GRADIENT, ora.PERIODIC)
     f1 = li.sod_fields(nx, 1, left=LEFT, right=RIGHT)
-    ref, _ = run_oracle(lat, gamma, tau, tau, (nx, 1), bc, f1, steps)
-    kappa = sensitivity(lat, gamma, tau, tau, (nx, 1), bc, f1, steps, 0, ref=ref)
+    E, _, ref, _ = run_variants(lat, gamma, tau, tau, (nx, 1), bc, f1, steps, 0)
     gpu, _ = run_gpu(0, gamma, tau, tau, (nx, 16), bc, li.sod_fields(nx, 16, left=LEFT, right=RIGHT), steps, 0)
     g0 = (gpu[0][:nx], gpu[1][:, :nx], gpu[2][:nx])
-    assert_parity(g0, ref, gamma, conditioned_tolerance(0, kappa, steps))
+    tol = spread_tolerance(0, E)
+    report(f"paper tube 2D 1000x16 gamma {gamma:.4g} FP64", assert_parity(g0, ref, gamma, tol), E, tol)
     _, _, r = ora.lattice_info(lat)
     e = l1_vs_exact(gpu, nx, gamma, steps, r)
     assert e[0] < 0.03 and e[1] < 0.02 and e[2] < 0.02, (gamma, e)
