@@ -63,7 +63,14 @@
  *  16  the arithmetic and the stored populations are FP32 (type real; the
  *      build adds -fsingle-precision-constant so that literals stay FP32);
  *      the velocity table is still solved in FP64 and rounded, and the
- *      grid totals of ora_conserved are still summed in FP64.
+ *      grid totals of ora_conserved are still summed in FP64;
+ *  32  the equilibrium is evaluated as a polynomial in s (Horner), its
+ *      coefficients collected from the same Hermite terms:
+ *        F_i / (w_i rho) = a0 + a1 s + a2 s^2 + s^3/6 + s^4/24,
+ *        a0 = 1 - u2/2 + t (x2 - D)/2 + u2^2/8 + t (D + 2 - x2) u2/4
+ *             + t^2 [x2^2 - 2 (D + 2) x2 + D (D + 2)]/8,
+ *        a1 = 1 - u2/2 + t (x2 - D - 2)/2,
+ *        a2 = 1/2 - u2/4 + t (x2 - D - 4)/4.
  * The default build (0) evaluates every expression exactly as written, in
  * FP64. */
 #ifndef ORA_VARIANT
@@ -74,6 +81,7 @@
 #define ORA_RELAX2 ((ORA_VARIANT) & 4)
 #define ORA_DEV ((ORA_VARIANT) & 8)
 #define ORA_F32 ((ORA_VARIANT) & 16)
+#define ORA_HORNER ((ORA_VARIANT) & 32)
 #if ORA_F32
 typedef float real;
 #define FMA_ fmaf
@@ -198,6 +206,48 @@ static int solve_dense(int n, double* A, double* b, double* x) {
   return 0;
 }
 
+/* Double-double numbers (hi + lo, |lo| <= ulp(hi)/2) for the residuals of
+ * the refinement: the error-free transformations of Knuth (two_sum) and of
+ * Dekker with a fused multiply-add (two_prod). */
+typedef struct { double hi, lo; } dd_t;
+
+static dd_t two_sum(double a, double b) {
+  dd_t r;
+  r.hi = a + b;
+  double bb = r.hi - a;
+  r.lo = (a - (r.hi - bb)) + (b - bb);
+  return r;
+}
+
+static dd_t two_prod(double a, double b) {
+  dd_t r;
+  r.hi = a * b;
+  r.lo = fma(a, b, -r.hi);
+  return r;
+}
+
+static dd_t dd_add(dd_t a, dd_t b) {
+  dd_t s = two_sum(a.hi, b.hi);
+  return two_sum(s.hi, s.lo + a.lo + b.lo);
+}
+
+static dd_t dd_mul(dd_t a, dd_t b) {
+  dd_t p = two_prod(a.hi, b.hi);
+  return two_sum(p.hi, p.lo + a.hi * b.lo + a.lo * b.hi);
+}
+
+/* Residual of one isotropy condition, r^deg sum_g w_g M_g - target, in
+ * double-double. */
+static double isotropy_residual(int G, const double* w, double r, int deg, const double* M,
+                                double target) {
+  dd_t sw = {0.0, 0.0};
+  for (int g = 0; g < G; ++g) sw = dd_add(sw, two_prod(w[g], M[g]));
+  dd_t rp = {1.0, 0.0};
+  for (int k = 0; k < deg; ++k) rp = dd_mul(rp, (dd_t){r, 0.0});
+  dd_t v = dd_add(dd_mul(rp, sw), (dd_t){-target, 0.0});
+  return v.hi + v.lo;
+}
+
 /* Build the velocity set of Table I / II and refine (r, w).
  *
  * Velocities: every integer vector in {-3..3}^D whose sorted absolute values
@@ -207,7 +257,12 @@ static int solve_dense(int n, double* A, double* b, double* x) {
  * Refinement: the unknowns are the G group weights and r; the conditions are
  * sum_i w_i (r c_i)^alpha = E[xi^alpha] of the unit Gaussian for the G+1
  * monomial classes listed above.  Newton's method with the exact Jacobian,
- * from the printed values. */
+ * from the printed values; then three more Newton corrections whose
+ * residuals are evaluated in double-double arithmetic.  The system is
+ * ill-conditioned in the smallest weights, so residuals in double leave
+ * the weights uncertain by up to 1e-13 relative (about a thousand ulps);
+ * with accurate residuals each correction removes the remaining error, and
+ * the result is the solution of the conditions rounded to double. */
 static int build_lattice(int lattice, ora_lattice_t* L) {
   memset(L, 0, sizeof(*L));
   if (lattice == ORA_D2Q37) { L->D = 2; L->G = 8; }
@@ -269,6 +324,19 @@ static int build_lattice(int lattice, ora_lattice_t* L) {
     }
     if (step < 1e-16) break;
   }
+  for (int it = 0; it < 3; ++it) {
+    double A[121], b[11], dx[11];
+    double r = x[G];
+    for (int k = 0; k < K; ++k) {
+      double sw = 0.0;
+      for (int g = 0; g < G; ++g) sw += x[g] * M[k][g];
+      b[k] = -isotropy_residual(G, x, r, deg[k], M[k], target[k]);
+      for (int g = 0; g < G; ++g) A[k * K + g] = ipow_(r, deg[k]) * M[k][g];
+      A[k * K + G] = (deg[k] > 0) ? deg[k] * ipow_(r, deg[k] - 1) * sw : 0.0;
+    }
+    if (solve_dense(K, A, b, dx)) return -3;
+    for (int k = 0; k < K; ++k) x[k] += dx[k];
+  }
   for (int g = 0; g < G; ++g) L->wg[g] = x[g];
   L->r = x[G];
   for (int i = 0; i < q; ++i) L->w[i] = L->wg[L->group[i]];
@@ -311,7 +379,14 @@ static void equilibrium(const ora_lattice_t* L, real rho, const real* u,
     real h4 = s * s * s * s - 6.0 * s * s * u2 + 3.0 * u2 * u2 +
               6.0 * t * (s * s * (x2 - D - 4.0) + (D + 2.0 - x2) * u2) +
               3.0 * t * t * (x2 * x2 - 2.0 * (D + 2.0) * x2 + D * (D + 2.0));
-#if ORA_REV
+#if ORA_HORNER
+    const real a0 = 1.0 - u2 / 2.0 + t * (x2 - D) / 2.0 + u2 * u2 / 8.0 + t * (D + 2.0 - x2) * u2 / 4.0 +
+                    t * t * (x2 * x2 - 2.0 * (D + 2.0) * x2 + D * (D + 2.0)) / 8.0;
+    const real a1 = 1.0 - u2 / 2.0 + t * (x2 - D - 2.0) / 2.0;
+    const real a2 = 0.5 - u2 / 4.0 + t * (x2 - D - 4.0) / 4.0;
+    (void)h0; (void)h1; (void)h2; (void)h3; (void)h4;
+    F[i] = (real)L->w[i] * rho * ((((s / 24.0 + 1.0 / 6.0) * s + a2) * s + a1) * s + a0);
+#elif ORA_REV
     F[i] = (real)L->w[i] * rho * (h4 / 24.0 + h3 / 6.0 + h2 / 2.0 + h1 + h0);
 #else
     F[i] = (real)L->w[i] * rho * (h0 + h1 + h2 / 2.0 + h3 / 6.0 + h4 / 24.0);

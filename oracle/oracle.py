@@ -26,11 +26,12 @@ LIB = os.path.join(HERE, "_build", "liblbm_oracle.so")
 # 1 reversed velocity order of every sum, 2 fused multiply-adds, 4 the
 # relaxation as (1 - 1/tau) q + Q_eq/tau, 8 populations held as deviations
 # from a reference equilibrium (Oracle.set_reference), 16 FP32 arithmetic and
-# storage.  They change rounding only; the tests use them as second checkers
+# storage, 32 the equilibrium as a polynomial in s (Horner).  They change
+# rounding only; the tests use them as second checkers
 # to measure how far correct evaluations of the scheme in FP64 (or in FP32)
 # land from the oracle on a flow.
-VARIANTS_F64 = (1, 2, 4, 7, 8, 15)
-VARIANTS_F32 = (16, 17, 18, 20, 23, 24, 31)
+VARIANTS_F64 = (1, 2, 4, 7, 8, 15, 32, 47)
+VARIANTS_F32 = (16, 17, 18, 20, 23, 24, 31, 48, 63)
 VARIANTS = VARIANTS_F64 + VARIANTS_F32
 
 D2Q37 = 0

@@ -44,8 +44,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         tag = "".join(d.split("=")[1] for d in defs)
         obj = os.path.join(obj_dir, os.path.splitext(src)[0] + tag + ".o")
         cmd = [NVCC, *ARCH, *FLAGS, *defs, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
-        if src.endswith(".cpp"):
-            cmd = [NVCC, *FLAGS, *defs, *extra, "-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
+        if src.endswith(".cpp"):  # host code: no contraction, so the double-double sums stay exact
+            cmd = [NVCC, *FLAGS, *defs, *extra, "-Xcompiler", "-ffp-contract=off", "-x", "c++", "-c",
+                   os.path.join(CSRC, src), "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{p.stdout}\n{p.stderr}")

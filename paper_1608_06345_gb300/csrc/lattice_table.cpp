@@ -10,7 +10,12 @@
 // Method: for a fixed r the conditions are linear in the group weights.
 // All conditions but x^8 determine w(r) by a dense solve; r is then the root
 // of the remaining x^8 condition, found by the secant method from [1.19, 1.20]
-// (the printed r is 1.19697977).
+// (the printed r is 1.19697977).  The conditions are ill-conditioned in the
+// smallest weights: solved with residuals in double, the weights are only
+// determined to about 1e-13 relative.  A final refinement therefore
+// evaluates the residuals of all G+1 conditions in double-double arithmetic
+// and corrects (w, r) with the Jacobian of the full system, which leaves the
+// solution of the conditions rounded to double.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -58,6 +63,33 @@ bool lu_solve(int n, double* a, double* b) {
   return true;
 }
 
+// Double-double values (hi + lo) for the residuals of the final refinement:
+// error-free sum (Knuth) and product (Dekker, with a fused multiply-add).
+struct DD {
+  double hi, lo;
+};
+
+DD dd_two_sum(double a, double b) {
+  const double s = a + b;
+  const double bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+DD dd_two_prod(double a, double b) {
+  const double p = a * b;
+  return {p, std::fma(a, b, -p)};
+}
+
+DD dd_add(DD a, DD b) {
+  const DD s = dd_two_sum(a.hi, b.hi);
+  return dd_two_sum(s.hi, s.lo + a.lo + b.lo);
+}
+
+DD dd_mul(DD a, DD b) {
+  const DD p = dd_two_prod(a.hi, b.hi);
+  return dd_two_sum(p.hi, p.lo + a.hi * b.lo + a.lo * b.hi);
+}
+
 struct Problem {
   const LatticeDef* L;
   int nlin;              // conditions solved linearly (= G)
@@ -100,6 +132,58 @@ bool weights_for(const Problem& P, double r, double* w, double* resid) {
   return true;
 }
 
+// integer moment of group g: sum over its members of c^alpha (exact)
+double group_moment_int(const LatticeDef& L, int g, const int* alpha) {
+  long long s = 0;
+  for (int i = 0; i < L.Q; ++i) {
+    if (L.grp[i] != g) continue;
+    long long m = 1;
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < alpha[a]; ++k) m *= L.c[i][a];
+    s += m;
+  }
+  return (double)s;
+}
+
+// Newton corrections of (w, r) on all G+1 conditions with residuals in
+// double-double: R_k = r^d_k sum_g w_g M_kg - target_k, J = dR/d(w, r).
+bool refine_dd(const Problem& P, double* w, double* r, int iters) {
+  const LatticeDef& L = *P.L;
+  const int G = P.nlin, K = G + 1;
+  double M[11][10];
+  int deg[11];
+  for (int k = 0; k < K; ++k) {
+    deg[k] = P.mono[k][0] + P.mono[k][1] + P.mono[k][2];
+    for (int g = 0; g < G; ++g) M[k][g] = group_moment_int(L, g, P.mono[k]);
+  }
+  for (int it = 0; it < iters; ++it) {
+    double a[121], b[11];
+    for (int k = 0; k < K; ++k) {
+      DD sw{0.0, 0.0};
+      double swd = 0.0;
+      for (int g = 0; g < G; ++g) {
+        sw = dd_add(sw, dd_two_prod(w[g], M[k][g]));
+        swd += w[g] * M[k][g];
+      }
+      DD rp{1.0, 0.0};
+      double rpd = 1.0, rpd1 = 1.0;  // r^d and r^(d-1) in double for the Jacobian
+      for (int q = 0; q < deg[k]; ++q) {
+        rp = dd_mul(rp, DD{*r, 0.0});
+        if (q + 1 < deg[k]) rpd1 *= *r;
+        rpd *= *r;
+      }
+      const DD res = dd_add(dd_mul(rp, sw), DD{-target(P.mono[k]), 0.0});
+      b[k] = -(res.hi + res.lo);
+      for (int g = 0; g < G; ++g) a[k * K + g] = rpd * M[k][g];
+      a[k * K + G] = deg[k] > 0 ? deg[k] * rpd1 * swd : 0.0;
+    }
+    if (!lu_solve(K, a, b)) return false;
+    for (int g = 0; g < G; ++g) w[g] += b[g];
+    *r += b[G];
+  }
+  return true;
+}
+
 }  // namespace
 
 static int build_lattice_table_uncached(int lattice, LatticeTable* out) {
@@ -131,6 +215,7 @@ static int build_lattice_table_uncached(int lattice, LatticeTable* out) {
     if (std::fabs(r1 - r0) <= 1e-16 * r1) break;
   }
   if (!weights_for(P, r1, w, &f1)) return -2;
+  if (!refine_dd(P, w, &r1, 3)) return -2;
   const LatticeDef& L = *P.L;
   out->D = L.D;
   out->Q = L.Q;

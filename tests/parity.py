@@ -53,6 +53,22 @@ def run_variants(lattice, gamma, tau_f, tau_g, shape, bc, fields, steps, prec, r
     return E, Ec, out, cref
 
 
+def library_reference(prec, rho0=0.0, T0=0.0):
+    """The reference state (rho0, T0) a library instance of precision prec
+    stores its populations against, for the rho0, T0 it was created with
+    (include/lbm.h): rho0 > 0 as given, rho0 < 0 whole storage (rho0 = 0),
+    otherwise whole storage for FP64 and rho0 = 1 for FP32; T0 <= 0 means 1.
+    The oracle's deviation variants take the same state (rho0 = 0 stores
+    whole: they then round as the oracle does)."""
+    if rho0 > 0:
+        r = rho0
+    elif rho0 < 0:
+        r = 0.0
+    else:
+        r = 0.0 if prec == 0 else 1.0
+    return r, (T0 if T0 > 0 else 1.0)
+
+
 def spread_tolerance(prec, E):
     """Tolerance of a case whose variant distance is E (run_variants):
     max(bar, 2 E).  The library is one more evaluation of the same

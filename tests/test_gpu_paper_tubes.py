@@ -22,7 +22,7 @@ import pytest
 import lbm_inputs as li
 from oracle import oracle as ora
 from oracle import riemann
-from tests.parity import assert_parity, report, run_gpu, run_variants, spread_tolerance
+from tests.parity import assert_parity, library_reference, report, run_gpu, run_variants, spread_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,8 @@ def test_paper_tube_3d_1000x16x16(prec):
     lat, nx, steps, gamma, tau = ora.D3Q107, 1000, 180, 1.4, 2.0 / 3.0
     bc = (ora.ZERO_GRADIENT, ora.PERIODIC, ora.PERIODIC)
     f1 = li.sod_fields(nx, 1, 1, D=3, left=LEFT, right=RIGHT)
-    E, _, ref, _ = run_variants(lat, gamma, tau, tau, (nx, 1, 1), bc, f1, steps, prec)
+    E, _, ref, _ = run_variants(lat, gamma, tau, tau, (nx, 1, 1), bc, f1, steps, prec,
+                                ref_state=library_reference(prec))
     gpu, _ = run_gpu(1, gamma, tau, tau, (nx, 16, 16), bc, li.sod_fields(nx, 16, 16, D=3, left=LEFT, right=RIGHT),
                      steps, prec)
     # uniform across the tube: every (y, z) row equals row 0 bitwise
@@ -61,7 +62,7 @@ def test_paper_tube_2d_gamma_sweep(gamma):
     lat, nx, steps, tau = ora.D2Q37, 1000, 180, 2.0 / 3.0
     bc = (ora.ZERO_GRADIENT, ora.PERIODIC)
     f1 = li.sod_fields(nx, 1, left=LEFT, right=RIGHT)
-    E, _, ref, _ = run_variants(lat, gamma, tau, tau, (nx, 1), bc, f1, steps, 0)
+    E, _, ref, _ = run_variants(lat, gamma, tau, tau, (nx, 1), bc, f1, steps, 0, ref_state=library_reference(0))
     gpu, _ = run_gpu(0, gamma, tau, tau, (nx, 16), bc, li.sod_fields(nx, 16, left=LEFT, right=RIGHT), steps, 0)
     g0 = (gpu[0][:nx], gpu[1][:, :nx], gpu[2][:nx])
     tol = spread_tolerance(0, E)

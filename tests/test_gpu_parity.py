@@ -15,7 +15,8 @@ import pytest
 
 import lbm_inputs as li
 from oracle import oracle as ora
-from tests.parity import TOL, assert_parity, report, run_gpu, run_oracle, run_variants, spread_tolerance
+from tests.parity import (TOL, assert_parity, library_reference, report, run_gpu, run_oracle, run_variants,
+                          spread_tolerance)
 
 pytestmark = pytest.mark.gpu
 
@@ -74,19 +75,20 @@ def rows_equal(q, nrows, nx):
     return bool(np.all(r == r[0]))
 
 
-def tube_parity(name, lat, shape, fields_full, fields_row, gamma, tau, steps, prec):
+def tube_parity(name, lat, shape, fields_full, fields_row, gamma, tau, steps, prec, rho0=0.0):
     """GPU run on the full tube cross-section; the oracle and its rounding
     variants on one row (the tube is uniform across, so every row of the GPU
     state must equal row 0 bitwise, and one row is the same computation per
     cell).  Fields, u and totals are compared against the variants'
-    spread."""
+    spread; the deviation variants take the instance's reference state."""
     nx = shape[0]
     nrows = int(np.prod(shape[1:]))
     D = len(shape)
     row = (nx,) + (1,) * (D - 1)
     bc = (ZG,) + (P,) * (D - 1)
-    E, Ec, ref, cref = run_variants(lat, gamma, tau, tau, row, bc, fields_row, steps, prec)
-    gpu, cgpu = run_gpu(lat, gamma, tau, tau, shape, bc, fields_full, steps, prec)
+    E, Ec, ref, cref = run_variants(lat, gamma, tau, tau, row, bc, fields_row, steps, prec,
+                                    ref_state=library_reference(prec, rho0))
+    gpu, cgpu = run_gpu(lat, gamma, tau, tau, shape, bc, fields_full, steps, prec, rho0=rho0)
     for q in (gpu[0], gpu[2], *gpu[1]):
         assert rows_equal(q, nrows, nx)
     g0 = (gpu[0][:nx], gpu[1][:, :nx], gpu[2][:nx])
@@ -103,16 +105,20 @@ def test_sod_tube_1000x4(steps, prec):
     """Classic Sod on 1000 x 4 (periodic y, zero-gradient x), gamma 1.4,
     tau_f = tau_g = 0.6 (the FP64 shock-tube workload).  The shock leaves
     through the open end near step 340 and the flow then amplifies
-    round-off, so the bar is the variants' spread (tube_parity)."""
+    round-off, so the bar is the variants' spread (tube_parity).  The
+    density spans a factor 8, so the populations are stored whole
+    (rho0 < 0; FP64's default): deviations from one reference state would
+    be up to 7 times the populations on the low-density side."""
     tube_parity(f"classic Sod 1000x4, {steps} steps", ora.D2Q37, (1000, 4), li.sod_fields(1000, 4),
-                li.sod_fields(1000, 1), 1.4, 0.6, steps, prec)
+                li.sod_fields(1000, 1), 1.4, 0.6, steps, prec, rho0=-1.0)
 
 
 @pytest.mark.parametrize("prec", [F64, F32])
 def test_sod_tube_3d_1024x4x4(prec):
-    """Classic Sod on the D3Q107 lattice, 1024 x 4 x 4, 100 steps."""
+    """Classic Sod on the D3Q107 lattice, 1024 x 4 x 4, 100 steps (whole
+    storage, as the 2D tube)."""
     tube_parity("classic Sod 3D 1024x4x4, 100 steps", ora.D3Q107, (1024, 4, 4), li.sod_fields(1024, 4, 4, D=3),
-                li.sod_fields(1024, 1, 1, D=3), 1.4, 0.6, 100, prec)
+                li.sod_fields(1024, 1, 1, D=3), 1.4, 0.6, 100, prec, rho0=-1.0)
 
 
 @pytest.mark.parametrize("prec", [F64, F32])

@@ -131,3 +131,26 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(lbm, "library_path", lambda: os.path.join(os.path.dirname(__file__), "no_such_liblbm.so"))
     with pytest.raises(ImportError, match="not built"):
         lbm.load()
+
+
+@pytest.mark.parametrize("lat", [0, 1])
+def test_library_table_is_the_exact_solution_rounded(lat):
+    """The library's refined (w, r) (its own solver: linear in w at fixed r,
+    a secant on r, then a double-double correction) equal the 50-digit
+    solution of the isotropy conditions rounded to double, to the last bit."""
+    pytest.importorskip("mpmath")
+    import ctypes
+
+    from paper_1608_06345_gb300 import lbm
+    from tests.isotropy_exact import exact_table, group_weights
+    D = 2 if lat == 0 else 3
+    q, r = ctypes.c_int(), ctypes.c_double()
+    c = np.zeros(107 * D, dtype=np.int32)
+    w = np.zeros(107)
+    assert lbm.load().lbm_lattice_table(lat, ctypes.byref(q), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(r)) == 0
+    Q = q.value
+    wg = group_weights(c[:Q * D].reshape(Q, D), w[:Q])
+    we, re_ = exact_table(lat, wg, r.value)
+    assert r.value == re_
+    assert np.array_equal(wg, we)

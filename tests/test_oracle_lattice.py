@@ -125,3 +125,18 @@ def test_gamma_delta_relation():
             assert math.isclose((d + D + 2) / (d + D), gamma, rel_tol=1e-14)
     assert math.isclose(ora.delta_from_gamma(2, 1.4), 3.0, rel_tol=1e-14)   # Sec. V, 2D
     assert math.isclose(ora.delta_from_gamma(3, 1.4), 2.0, rel_tol=1e-14)   # Sec. V, 3D
+
+
+@pytest.mark.parametrize("lat", [ora.D2Q37, ora.D3Q107])
+def test_refined_table_is_the_exact_solution_rounded(lat):
+    """The oracle's refined (w, r) equal the solution of the isotropy
+    conditions solved at 50 digits and rounded to double, to the last bit:
+    the refinement's double-double residuals leave no algorithm-dependent
+    error (reading R3)."""
+    pytest.importorskip("mpmath")
+    from tests.isotropy_exact import exact_table, group_weights
+    c, w, r = ora.lattice_info(lat)
+    wg = group_weights(c, w)
+    we, re_ = exact_table(lat, wg, r)
+    assert r == re_
+    assert np.array_equal(wg, we)

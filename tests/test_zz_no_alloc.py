@@ -31,8 +31,11 @@ def device_state(solver):
     return torch.from_numpy(raw).cuda()
 
 
+# (300, 50) spans 4 blocks of 4096 cells with a partial last block; 4096^2 is
+# the maximum, 4096 full blocks
 @pytest.mark.parametrize("lat,shape,prec", [(0, (300, 7), 0), (1, (40, 6, 5), 0), (0, (257, 9), 1),
-                                            (0, (300, 7), 2), (1, (20, 6, 5), 3)])
+                                            (0, (300, 7), 2), (1, (20, 6, 5), 3), (0, (300, 50), 1),
+                                            (1, (30, 20, 25), 0), (0, (4096, 4096), 2)])
 def test_noalloc_totals_match_lbm_conserved_twice(lat, shape, prec):
     import torch
 
@@ -60,3 +63,44 @@ def test_noalloc_rejects_sizes_above_its_maximum():
         lbm.lbm_conserved_noalloc(0, 1, 1.4, 1 << 20, too_many, too_many)
     assert ei.value.code == lbm.LBM_EINVAL
     assert "maximum" in str(ei.value)
+
+
+def _state_and_args():
+    from paper_1608_06345_gb300 import lbm
+    s = lbm.Solver(0, 1.4, 0.6, 0.6, (64, 4), prec=1)
+    s.init(*li.random_fields(256, 2, seed=1))
+    return s, device_state(s)
+
+
+def test_noalloc_rejects_a_misaligned_state():
+    """A state pointer off its 4-byte storage word is refused on the host,
+    before anything is launched."""
+    import torch
+
+    from paper_1608_06345_gb300 import lbm
+    s, state = _state_and_args()
+    torch.cuda.synchronize()
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_conserved_noalloc(0, 1, 1.4, state.data_ptr() + 2, 256, 256)
+    assert ei.value.code == lbm.LBM_EINVAL and "aligned" in str(ei.value)
+
+
+def test_noalloc_rejects_host_memory():
+    """A host pointer is refused on the host (cudaPointerGetAttributes); the
+    host buffer covers the whole extent all the same."""
+    from paper_1608_06345_gb300 import lbm
+    host = np.zeros(2 * 37 * 256, dtype=np.float32)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_conserved_noalloc(0, 1, 1.4, host.ctypes.data, 256, 256)
+    assert ei.value.code == lbm.LBM_EINVAL
+
+
+def test_binding_rejects_a_short_tensor():
+    import torch
+
+    from paper_1608_06345_gb300 import lbm
+    short = torch.zeros(2 * 37 * 256 - 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_conserved_noalloc(0, 1, 1.4, short, 256, 256)
+    assert ei.value.code == lbm.LBM_EINVAL
+
