@@ -74,10 +74,25 @@ typedef struct {
                            bytes, 256-byte aligned; NULL = the library allocates */
   size_t device_bytes;  /* size of device_mem */
   double rho0, T0;      /* reference state (rho0, u = 0, T0) whose equilibrium the
-                           stored populations are deviations from; 0 means 1.0.
-                           Exact for every precision; for 16-bit storage pick it
-                           near the flow's mean state */
+                           stored populations are deviations from (see below) */
 } lbm_grid;
+
+/* The reference state.  The populations are stored as deviations
+ * g_i - gref_i, h_i - href_i from the equilibrium gref_i = F_i(rho0, 0, T0),
+ * href_i = (delta/2) T0 gref_i: an exact change of variables that changes
+ * only the rounding.  Where the flow is near the reference the deviations
+ * are small and keep more bits than the populations (FP32 resolves the
+ * momentum of a flow near rest about 50 times better); where it is far from
+ * it (|g - gref| > |g|, e.g. a density below half of rho0) they keep fewer,
+ * about log2(|g - gref| / |g|) bits fewer.
+ *   rho0 > 0      that reference;
+ *   rho0 < 0      no reference, populations stored whole (gref = 0): FP64
+ *                 and FP32 storage only;
+ *   rho0 = 0, NaN the precision's default: whole storage for LBM_F64,
+ *                 rho0 = 1 for LBM_F32 and 16-bit storage.
+ * T0 that is not positive (NaN included) means 1.0.  16-bit storage needs a
+ * reference near the flow's state (the codec stores (g - gref)/gref); a
+ * negative rho0 there fails with LBM_EINVAL. */
 
 /* Device bytes an instance needs: two copies of the 2Q population planes
  * (double buffer) plus a small tail (error word, reduction partials).
@@ -155,8 +170,9 @@ long lbm_steps_done(lbm_handle h);
  *  - 16-bit storage: Q planes of N 4-byte pairs (g_i in the low 16 bits, h_i
  *    in the high 16 bits), the values (g_i - gref_i)/gref_i and
  *    (h_i - href_i)/hscale_i.
- * gref_i = F_i(rho0, u = 0, T0) is the instance's reference equilibrium,
- * href_i = (delta/2) T0 gref_i, hscale_i = href_i (gref_i when delta = 0). */
+ * gref_i = F_i(rho0, u = 0, T0) is the instance's reference equilibrium
+ * (zero for whole storage), href_i = (delta/2) T0 gref_i, hscale_i = href_i
+ * (gref_i when delta = 0). */
 size_t lbm_raw_state_bytes(lbm_handle h);
 int lbm_get_state(lbm_handle h, void* host, size_t bytes);
 int lbm_set_state(lbm_handle h, const void* host, size_t bytes);
@@ -176,33 +192,43 @@ int lbm_lattice_table(int lattice, int* q, int* c, double* w, double* r);
  *  state         device pointer to the planes in the layout of lbm_get_state
  *                (deviations from the reference equilibrium of rho0, T0);
  *                plane p starts plane_stride elements (pairs, for 16-bit
- *                storage) after plane p - 1
+ *                storage) after plane p - 1.  It must be memory of the
+ *                current device (or managed memory) and aligned to the
+ *                storage word (8 bytes for FP64, 4 bytes otherwise); host
+ *                pointers, other devices' memory and misaligned pointers
+ *                fail with LBM_EINVAL before anything is launched.  The
+ *                caller guarantees that the planes' extent, (2Q-1)
+ *                plane_stride + ncells elements (Q-1 and pairs for 16-bit
+ *                storage), lies inside the allocation
  *  ncells        cells per plane, 0 <= ncells <= 16777216 (4096^2 or 256^3);
  *                larger sizes fail with LBM_EINVAL
- *  lattice, prec, gamma, rho0, T0: as given to lbm_create (rho0, T0 <= 0
- *                mean 1.0)
+ *  lattice, prec, gamma, rho0, T0: as given to lbm_create (the same
+ *                defaults: see the reference state above)
  *  stream        cudaStream_t to run on (NULL = default stream); the call
  *                synchronises it before returning
  *  out           host array of D + 2 doubles
  * The block partials live in one static device array of about 160 KB that
  * every GPU loading the library keeps until exit.  The first call on a
  * device looks up that array's device address (make it before any stream
- * capture).  All calls share the array: calls that overlap on the GPU race
- * and give wrong totals.  No cudaMalloc, cudaFree or allocating library
- * routine is called. */
+ * capture).  That address is kept per device index for the life of the
+ * process; after a cudaDeviceReset the array is mapped anew, so a process
+ * that resets a device must not call this entry point again.  All calls
+ * share the array: calls that overlap on the GPU race and give wrong
+ * totals.  No cudaMalloc, cudaFree or allocating library routine is called. */
 int lbm_conserved_noalloc(int lattice, int prec, double gamma, double rho0, double T0, const void* state,
                           long long ncells, long long plane_stride, void* stream, double* out);
 
 /* Launch shapes of the step kernel (execution control with no counterpart in
- * the paper; every shape computes the same step, the stage-4 and stage-7
+ * the paper; every shape computes the same step, the stage-4, 7 and 8
  * shapes up to the summation order of the moments).  Each (lattice, precision) has a small
  * table of compiled candidates (how the pulled values are staged --
  * registers, shared memory by cp.async, g in registers and h in shared
  * memory (stages 0-3), the velocities of each cell split over 4 warps
  * (stage 4; stage 7 with the per-cell equilibrium coefficients formed once
- * and shared), or, for 16-bit storage, the (g, h) pairs held packed in
- * registers (stage 6) -- and the cells per thread block); index 0 is the
- * default.
+ * and shared), for 16-bit storage the (g, h) pairs held packed in registers
+ * (stage 6), or two lanes per cell, one for c and one for -c of every
+ * (c, -c) pair, whose moment sums meet by warp shuffles (stage 8) -- and
+ * the cells per thread block); index 0 is the default.
  * lbm_shape_info describes candidate `index` (LBM_EINVAL past the end). */
 int lbm_shape_info(int lattice, int prec, int index, int* stage, int* block);
 

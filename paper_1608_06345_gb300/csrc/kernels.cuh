@@ -890,6 +890,271 @@ __global__ void __launch_bounds__(32 * P, MINB) k_step_split(const S* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// the mirror-pair step (STAGE 8): every cell is worked by two lanes of one
+// warp, lane l and lane l ^ 16.  The lower half-warp (half 0, sign +1) takes
+// the member c of each (c, -c) pair and the rest velocity; the upper half
+// (half 1, sign -1) takes the member -c.  Both halves run one instruction
+// stream:
+//   - the pull of -c reads x + c, so the sign is folded into the 7-entry
+//     offset tables of each axis, and the member -c lies one plane after c;
+//   - s(-c; u) = s(c; -u): with u negated the pair's even part e(s^2) is the
+//     same and the odd part flips, so each half stores e + o with its own
+//     sign of u;
+//   - the five moment sums of the halves meet by one __shfl_xor_sync each;
+//     both lanes add (or subtract) the two halves' partial sums in the same
+//     operand order, so they hold bitwise identical moments.
+// A thread holds the (Q + 1) / 2 pulled (g, h) of its half instead of Q, so
+// about twice the warps fit per SM; the pair's even and odd parts are formed
+// by both lanes.  A block of BX threads covers BX / 2 cells of a row; lanes
+// past the row end pull from a valid cell, take part in the shuffles and
+// store nothing.
+// ---------------------------------------------------------------------------
+template <int LAT, class S, class C, int BX, int MINB, bool IDX32, bool HS>
+__global__ void __launch_bounds__(BX, MINB) k_step_mirror(const S* __restrict__ src, S* __restrict__ dst,
+                                                         const Args<C> a) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  constexpr int NP = (Q - 1) / 2;  // (c, -c) pairs; pair k is velocities 2k+1 (c) and 2k+2 (-c)
+  constexpr bool SCALED = IsS16<S>::value;
+  static_assert(BX % 32 == 0, "whole warps");
+  static_assert(!(HS && SCALED), "16-bit pairs are held packed in registers");
+  const int lane = threadIdx.x & 31;
+  const int half = lane >> 4;
+  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+  const int x = blockIdx.x * (BX / 2) + (threadIdx.x >> 5) * 16 + (lane & 15);
+  const int y = blockIdx.y, z = blockIdx.z;
+  const bool active = x < nx;
+  const int xs = active ? x : nx - 1;
+  const int sg = half ? -1 : 1;
+  // source offsets of the pull of sg * c for c = -3..3 (index c + 3)
+  unsigned xo[7], yo[7], zo[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    xo[k] = (unsigned)pull_coord(xs, sg * (k - 3), nx, a.bc[0]);
+    yo[k] = (unsigned)pull_coord(y, sg * (k - 3), ny, a.bc[1]) * (unsigned)nx;
+    zo[k] = (L::D == 3) ? (unsigned)pull_coord(z, sg * (k - 3), nz, a.bc[2]) * (unsigned)nx * (unsigned)ny : 0u;
+  }
+  const unsigned cell = (unsigned)xs + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+  const long long ps = a.ps;
+  // element index of this half's member in plane `plane` (pair index for
+  // 16-bit storage) at cell offset off
+  auto eidx = [&](int plane, unsigned off) -> size_t {
+    if constexpr (IDX32) return (size_t)((unsigned)(plane + half) * (unsigned)ps + off);
+    else return (size_t)(plane + half) * (size_t)ps + off;
+  };
+  // the pulled values: FP32/FP64 g in registers and h in registers or (HS)
+  // in shared memory slots [k][thread] filled by cp.async; 16-bit storage
+  // the packed (g, h) pairs in registers.  The rest velocity is pulled by
+  // half 0 only (half 1 keeps zeros).
+  C g0 = C(0), h0 = C(0);
+  C g[SCALED ? 1 : NP];
+  C h[(SCALED || HS) ? 1 : NP];
+  unsigned pr[SCALED ? NP : 1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* shh = reinterpret_cast<S*>(smem_raw);  // HS: [NP][BX]
+  if (half == 0) {
+    if constexpr (SCALED) {
+      float lo, hi;
+      unpack16<S>(__ldg(reinterpret_cast<const unsigned*>(src) + (size_t)cell), lo, hi);
+      g0 = lo;
+      h0 = hi;
+    } else {
+      g0 = static_cast<C>(ldg_s(src + (size_t)cell));
+      h0 = static_cast<C>(ldg_s(src + (size_t)Q * (size_t)ps + cell));
+    }
+  }
+  static_for<NP>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int i = 2 * k + 1;
+    const unsigned off = zo[L::cz(i) + 3] + yo[L::cy(i) + 3] + xo[L::cx(i) + 3];
+    if constexpr (SCALED) {
+      pr[k] = __ldg(reinterpret_cast<const unsigned*>(src) + eidx(i, off));
+    } else {
+      if constexpr (HS) {
+        static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(shh + k * BX + threadIdx.x);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(src + eidx(Q + i, off)),
+                     "n"(sizeof(S)));
+      } else {
+        h[k] = static_cast<C>(ldg_s(src + eidx(Q + i, off)));
+      }
+      g[k] = static_cast<C>(ldg_s(src + eidx(i, off)));
+    }
+  });
+  if constexpr (HS) asm volatile("cp.async.wait_all;\n" ::: "memory");
+  // accessors of the pulled g, h of pair k (16-bit: the stored relative
+  // deviations, unpacked where they are used; HS: h re-read from shared
+  // memory by each pass)
+  const volatile S* shv = shh;
+  auto getg = [&](int k) -> C {
+    if constexpr (SCALED) {
+      float lo, hi;
+      unpack16<S>(pr[k], lo, hi);
+      return static_cast<C>(lo);
+    } else {
+      return g[k];
+    }
+  };
+  auto geth = [&](int k) -> C {
+    if constexpr (SCALED) {
+      float lo, hi;
+      unpack16<S>(pr[k], lo, hi);
+      return static_cast<C>(hi);
+    } else if constexpr (HS) {
+      return static_cast<C>(shv[k * BX + threadIdx.x]);
+    } else {
+      return h[k];
+    }
+  };
+  // this half's partial sums, with the member c's components (for half 1
+  // the momentum sums are minus its share)
+  C m, H, jx = C(0), jy = C(0), jz = C(0), k2 = C(0);
+  if constexpr (SCALED) {
+    m = a.gref[0] * g0;
+    H = a.hscale[0] * h0;
+  } else {
+    m = g0;
+    H = h0;
+  }
+  {
+    C s1 = C(1), sc2 = C(0), sh = C(1);
+    static_for<NP>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      constexpr int i = 2 * k + 1;
+      constexpr int gr = L::grp(i);
+      const C gk = getg(k), hk = geth(k);
+      if constexpr (SCALED) {
+        if constexpr (k == 0 || L::grp(i - 2) != gr) {
+          s1 = a.gref[gr];
+          sc2 = C(L::c2(i)) * s1;
+          sh = a.hscale[gr];
+        }
+        const C gv = s1 * gk;
+        m += gv;
+        if constexpr (L::cx(i) != 0) jx = fma(C(L::cx(i)), gv, jx);
+        if constexpr (L::cy(i) != 0) jy = fma(C(L::cy(i)), gv, jy);
+        if constexpr (L::cz(i) != 0) jz = fma(C(L::cz(i)), gv, jz);
+        k2 = fma(sc2, gk, k2);
+        H = fma(sh, hk, H);
+      } else {
+        m += gk;
+        if constexpr (L::cx(i) != 0) jx = fma(C(L::cx(i)), gk, jx);
+        if constexpr (L::cy(i) != 0) jy = fma(C(L::cy(i)), gk, jy);
+        if constexpr (L::cz(i) != 0) jz = fma(C(L::cz(i)), gk, jz);
+        k2 = fma(C(L::c2(i)), gk, k2);
+        H += hk;
+      }
+    });
+    (void)s1;
+    (void)sc2;
+    (void)sh;
+  }
+  const C e4 = fma(a.half_r2, k2, H);
+  // combine the halves: lower + upper for the even sums, lower - upper for
+  // the momentum; both lanes evaluate the same operation on the same operands
+  C acc[5];
+  {
+    const C own[5] = {m, jx, jy, jz, e4};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if (q == 3 && L::D == 2) {
+        acc[q] = C(0);
+        continue;
+      }
+      const C other = __shfl_xor_sync(0xffffffffu, own[q], 16);
+      const C lo = half ? other : own[q];
+      const C up = half ? own[q] : other;
+      acc[q] = (q >= 1 && q <= 3) ? lo - up : lo + up;
+    }
+  }
+  C drho, u[3], dT;
+  moments_finish<LAT, C>(acc, a, drho, u, dT);
+  if (active && half == 0 && !(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+  if constexpr (SCALED) {
+    // an empty asm that claims to change each pair: the relaxation pass
+    // unpacks again instead of keeping the moments pass's unpacked values
+    // alive (it emits no instruction)
+    static_for<NP>([&](auto K) { asm volatile("" : "+r"(pr[decltype(K)::value])); });
+  }
+  EqCoef<LAT, C> kc;
+  eq_coeffs<LAT, C>(drho, u, dT, a, kc);
+  // this half's sign of u: s of the member -c is s(c) at -u
+#pragma unroll
+  for (int q = 0; q < 3; ++q) kc.ur[q] = half ? -kc.ur[q] : kc.ur[q];
+  // relax and store
+  const C hA = a.omega_g * a.half_delta * kc.T;
+  const C om1 = C(1) - a.omega_g;
+  const C hbs = a.omega_g * a.half_delta * kc.dT;
+  auto store = [&](int i, unsigned plane_half, C gn, C hn) {
+    // the stored plane is i + plane_half
+    if constexpr (SCALED) {
+      unsigned* dp = reinterpret_cast<unsigned*>(dst);
+      const unsigned pv = pack16<S>(static_cast<float>(gn), static_cast<float>(hn));
+      if constexpr (IDX32) dp[(unsigned)(i + plane_half) * (unsigned)ps + cell] = pv;
+      else dp[(size_t)(i + plane_half) * ps + cell] = pv;
+    } else {
+      if constexpr (IDX32) {
+        dst[(unsigned)(i + plane_half) * (unsigned)ps + cell] = static_cast<S>(gn);
+        dst[(unsigned)(Q + i + plane_half) * (unsigned)ps + cell] = static_cast<S>(hn);
+      } else {
+        dst[(size_t)(i + plane_half) * ps + cell] = static_cast<S>(gn);
+        dst[(size_t)(Q + i + plane_half) * ps + cell] = static_cast<S>(hn);
+      }
+    }
+  };
+  // per group: the equilibrium coefficients c0..c4 and the relaxation's
+  // constants (ig = 1/gref, hAs = hA/hscale, hbg = hbs gref/hscale for
+  // 16-bit storage; hAs = hA, hbg = hbs gref otherwise)
+  C c0, c1, c2, c3, c4, ig, hAs, hbg;
+  auto group = [&](int gr) {
+    const C x2 = a.x2g[gr];
+    const C P = fma(x2, fma(x2, kc.pc, kc.pb), kc.pa);
+    const C W = a.wg[gr] * kc.rho;
+    c0 = a.wg[gr] * fma(kc.drho, C(1) + P, a.rho0 * (P - a.pref[gr]));
+    c1 = W * fma(kc.be1, x2, kc.be0);
+    c2 = W * fma(kc.ga1, x2, kc.ga0);
+    c3 = W * C(1.0 / 6.0);
+    c4 = W * C(1.0 / 24.0);
+    if constexpr (SCALED) {
+      ig = a.inv_gref[gr];
+      hAs = hA * a.inv_hscale[gr];
+      hbg = hbs * a.gref[gr] * a.inv_hscale[gr];
+    } else {
+      ig = C(1);
+      hAs = hA;
+      hbg = hbs * a.gref[gr];
+    }
+  };
+  auto relax = [&](C dF, C gv, C hv, C& gn, C& hn) {
+    if constexpr (SCALED) gn = fma(a.omega_f, fma(dF, ig, -gv), gv);
+    else gn = fma(a.omega_f, dF - gv, gv);
+    hn = fma(hAs, dF, fma(om1, hv, hbg));
+  };
+  group(0);
+  if (active && half == 0) {
+    C gn, hn;
+    relax(c0, g0, h0, gn, hn);
+    store(0, 0u, gn, hn);
+  }
+  static_for<NP>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int i = 2 * k + 1;
+    constexpr int gr = L::grp(i);
+    if constexpr (k == 0 || L::grp(i - 2) != gr) group(gr);
+    C s = C(0);
+    if constexpr (L::cx(i) != 0) s = fma(C(L::cx(i)), kc.ur[0], s);
+    if constexpr (L::cy(i) != 0) s = fma(C(L::cy(i)), kc.ur[1], s);
+    if constexpr (L::cz(i) != 0) s = fma(C(L::cz(i)), kc.ur[2], s);
+    const C s2 = s * s;
+    const C e = fma(s2, fma(s2, c4, c2), c0);
+    const C o = s * fma(s2, c3, c1);
+    C gn, hn;
+    relax(e + o, getg(k), geth(k), gn, hn);
+    if (active) store(i, (unsigned)half, gn, hn);
+  });
+}
+
+// ---------------------------------------------------------------------------
 // the finite-difference variant of Sec. III (Eq. (16)/(17) with the
 // convection term discretised along each axis by the third-order upwind
 // difference; the printed g_j is read as g_i), lamr = lambda r, lambda = dt/dx:

@@ -72,31 +72,68 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
   return cudaGetLastError();
 }
 
+// the mirror-pair step (stage 8): BX threads, BX / 2 cells per block; HS
+// stages h in shared memory (FP32/FP64 storage)
+template <int LAT, class S, class C, int BX, int MINB, bool HS, bool IDX32>
+cudaError_t launch_step_mirror_v(const Instance* inst, const void* src, void* dst, const Args<C>& a,
+                                 bool configure_only) {
+  constexpr size_t smem = HS ? sizeof(S) * ((Lat<LAT>::Q - 1) / 2) * BX : 0;
+  if constexpr (smem > 48 * 1024) {
+    // per-device shared-memory opt-in, as in launch_step_v
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || !(configured.load(std::memory_order_acquire) & (1ull << dev))) {
+      e = cudaFuncSetAttribute(k_step_mirror<LAT, S, C, BX, MINB, IDX32, HS>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      if (dev < 64) configured.fetch_or(1ull << dev, std::memory_order_release);
+    }
+  }
+  if (configure_only) return cudaSuccess;
+  const dim3 grid((unsigned)((inst->n[0] + BX / 2 - 1) / (BX / 2)), (unsigned)inst->n[1], (unsigned)inst->n[2]);
+  k_step_mirror<LAT, S, C, BX, MINB, IDX32, HS><<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src),
+                                                                                 static_cast<S*>(dst), a);
+  return cudaGetLastError();
+}
+
+template <int LAT, class S, class C, int BX, int MINB, bool HS>
+cudaError_t launch_step_mirror(const Instance* inst, const void* src, void* dst, const Args<C>& a,
+                               bool configure_only = false) {
+  const long long planes = IsS16<S>::value ? Lat<LAT>::Q : 2LL * Lat<LAT>::Q;
+  if (planes * inst->ps < (1LL << 32))
+    return launch_step_mirror_v<LAT, S, C, BX, MINB, HS, true>(inst, src, dst, a, configure_only);
+  return launch_step_mirror_v<LAT, S, C, BX, MINB, HS, false>(inst, src, dst, a, configure_only);
+}
+
 // Candidate shapes of the step per (lattice, storage), tried by the
 // autotuner; index 0 is the default.  (stage, cells per block, minimum
 // resident blocks per SM requested from the compiler, which caps registers):
 //   D2Q37 FP32:        (0,128,4) (0,256,2) (0,64,8) (0,128,1)
 //   D2Q37 16-bit:      (6,128,8) (6,128,7) (6,128,6) (6,256,3) (0,128,4) (0,64,8)
 //   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)  (4,32,4)  (7,32,4)
-//   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)
+//   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)  (8,32,8)  (8,64,4)
 //   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)  (7,32,3)
-//   D3Q107 16-bit:     (6,64,6)  (2,64,8)  (2,64,1)  (4,32,6)
+//   D3Q107 16-bit:     (6,64,6)  (2,64,8)  (2,64,1)  (4,32,6)  (8,32,10) (8,32,12)
 // Stage 4 is the velocity-split step: 4 warps per block of 32 cells; stage 7
-// the same with the per-cell coefficients formed once by warp 0 and shared.  Its
-// moments are summed in another order, so its results differ from the
+// the same with the per-cell coefficients formed once by warp 0 and shared.
+// Stage 8 is the mirror-pair step: two lanes per cell (c and -c of every
+// pair), h staged in shared memory for FP32.  The moments of stages 4, 7
+// and 8 are summed in another order, so their results differ from the
 // other shapes' by rounding; the defaults (index 0) are the shapes the
 // batched pool uses, whose results are bitwise those of a lone instance.
 template <int LAT, class S>
 struct StepShapes {
   static constexpr int count =
-      (LAT == 0) ? (sizeof(S) == 8 ? 5 : (sizeof(S) == 2 ? 6 : 4)) : (sizeof(S) == 8 ? 4 : 4);
+      (LAT == 0) ? (sizeof(S) == 8 ? 5 : (sizeof(S) == 2 ? 6 : 4)) : (sizeof(S) == 8 ? 4 : 6);
   static void get(int k, int* stage, int* bx, int* minb) {
     static const int s2[4][3] = {{0, 128, 4}, {0, 256, 2}, {0, 64, 8}, {0, 128, 1}};
     static const int s2h[6][3] = {{6, 128, 8}, {6, 128, 7}, {6, 128, 6}, {6, 256, 3}, {0, 128, 4}, {0, 64, 8}};
     static const int s2d[5][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}, {4, 32, 4}, {7, 32, 4}};
-    static const int s3f[4][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}};
+    static const int s3f[6][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}, {8, 32, 8}, {8, 64, 4}};
     static const int s3d[4][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}, {7, 32, 3}};
-    static const int s3h[4][3] = {{6, 64, 6}, {2, 64, 8}, {2, 64, 1}, {4, 32, 6}};
+    static const int s3h[6][3] = {{6, 64, 6}, {2, 64, 8}, {2, 64, 1}, {4, 32, 6}, {8, 32, 10}, {8, 32, 12}};
     const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : (sizeof(S) == 2 ? s2h : s2))
                                   : (sizeof(S) == 4 ? s3f : (sizeof(S) == 8 ? s3d : s3h));
     *stage = t[k][0];
@@ -147,6 +184,8 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
       case 1: return launch_step_t<LAT, S, C, 3, 64>(inst, src, dst, a, configure_only);
       case 2: return launch_step_t<LAT, S, C, 1, 64>(inst, src, dst, a, configure_only);
       case 3: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
+      case 4: return launch_step_mirror<LAT, S, C, 64, 8, true>(inst, src, dst, a, configure_only);
+      case 5: return launch_step_mirror<LAT, S, C, 128, 4, true>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 3, 64, 6>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (sizeof(S) == 8) {
@@ -161,6 +200,8 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
       case 1: return launch_step_t<LAT, S, C, 2, 64, 8>(inst, src, dst, a, configure_only);
       case 2: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a, configure_only);
       case 3: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
+      case 4: return launch_step_mirror<LAT, S, C, 64, 10, false>(inst, src, dst, a, configure_only);
+      case 5: return launch_step_mirror<LAT, S, C, 64, 12, false>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 6, 64, 6>(inst, src, dst, a, configure_only);
     }
   }

@@ -24,6 +24,42 @@ __global__ void k_conserve_final(const double* __restrict__ partial, int nblocks
   if (lane == 0) out[k] = s;
 }
 
+int resolve_reference(int prec, double rho0, double T0, double* rho0_out, double* T0_out) {
+  const bool s16 = (prec == kF32S16F || prec == kF32S16BF);
+  double r;
+  if (rho0 > 0.0 && std::isfinite(rho0)) {
+    r = rho0;
+  } else if (rho0 < 0.0) {
+    if (s16) return LBM_EINVAL;  // the 16-bit codec scales by the reference
+    r = 0.0;
+  } else {  // 0 or NaN: the precision's default
+    r = (prec == kF64) ? 0.0 : 1.0;
+  }
+  *rho0_out = r;
+  *T0_out = (T0 > 0.0 && std::isfinite(T0)) ? T0 : 1.0;
+  return LBM_OK;
+}
+
+// Reference equilibrium of the instance per velocity group, Eq. (18) at
+// (rho0, u = 0, T0): gref = w rho0 (1 + pref) with
+// pref = t0 (x2 - D)/2 + t0^2 [x2^2 - 2 (D + 2) x2 + D (D + 2)] / 8, t0 = T0 - 1;
+// the 16-bit h codec scales by href = (delta/2) T0 gref (by gref if delta = 0).
+void reference_constants(const LatticeTable& t, double delta, double rho0, double T0, double* gref,
+                         double* pref, double* hscale) {
+  const double D = t.D, th = T0 - 1.0;
+  for (int g = 0; g < 10; ++g) {
+    if (g >= t.G) {
+      gref[g] = hscale[g] = 1.0;
+      pref[g] = 0.0;
+      continue;
+    }
+    const double x2 = t.x2g[g];
+    pref[g] = 0.5 * th * (x2 - D) + 0.125 * th * th * (x2 * x2 - 2.0 * (D + 2.0) * x2 + D * (D + 2.0));
+    gref[g] = t.wg[g] * rho0 * (1.0 + pref[g]);
+    hscale[g] = (delta > 0.0) ? 0.5 * delta * T0 * gref[g] : gref[g];
+  }
+}
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -69,26 +105,6 @@ size_t buffer_bytes(int Q, long long N, int prec) {
   return round_up(2 * (size_t)Q * ps * word_of(prec), 256);
 }
 
-// Reference equilibrium of the instance per velocity group, Eq. (18) at
-// (rho0, u = 0, T0): gref = w rho0 (1 + pref) with
-// pref = t0 (x2 - D)/2 + t0^2 [x2^2 - 2 (D + 2) x2 + D (D + 2)] / 8, t0 = T0 - 1;
-// the 16-bit h codec scales by href = (delta/2) T0 gref (by gref if delta = 0).
-void reference_constants(const LatticeTable& t, double delta, double rho0, double T0, double* gref,
-                         double* pref, double* hscale) {
-  const double D = t.D, th = T0 - 1.0;
-  for (int g = 0; g < 10; ++g) {
-    if (g >= t.G) {
-      gref[g] = hscale[g] = 1.0;
-      pref[g] = 0.0;
-      continue;
-    }
-    const double x2 = t.x2g[g];
-    pref[g] = 0.5 * th * (x2 - D) + 0.125 * th * th * (x2 * x2 - 2.0 * (D + 2.0) * x2 + D * (D + 2.0));
-    gref[g] = t.wg[g] * rho0 * (1.0 + pref[g]);
-    hscale[g] = (delta > 0.0) ? 0.5 * delta * T0 * gref[g] : gref[g];
-  }
-}
-
 template <class C>
 void fill_args(const Instance& I, Args<C>* a) {
   std::memset(a, 0, sizeof(*a));
@@ -115,9 +131,9 @@ void fill_args(const Instance& I, Args<C>* a) {
     a->x2g[g] = (C)I.table.x2g[g];
     a->gref[g] = (C)gref[g];
     a->pref[g] = (C)pref[g];
-    a->inv_gref[g] = (C)(1.0 / gref[g]);
+    a->inv_gref[g] = (C)(gref[g] != 0.0 ? 1.0 / gref[g] : 0.0);  // 0: whole storage (16-bit codec unused)
     a->hscale[g] = (C)hscale[g];
-    a->inv_hscale[g] = (C)(1.0 / hscale[g]);
+    a->inv_hscale[g] = (C)(hscale[g] != 0.0 ? 1.0 / hscale[g] : 0.0);
   }
   a->flag = I.flag;
 }
@@ -189,8 +205,8 @@ int prepare_instance(Instance* I, int lattice, double gamma, double tau_f, doubl
   I->delta = delta;
   I->tau_f = tau_f;
   I->tau_g = tau_g;
-  I->rho0 = grid->rho0 > 0.0 ? grid->rho0 : 1.0;
-  I->T0 = grid->T0 > 0.0 ? grid->T0 : 1.0;
+  if (resolve_reference(grid->prec, grid->rho0, grid->T0, &I->rho0, &I->T0) != LBM_OK)
+    return fail(LBM_EINVAL, "16-bit storage needs a positive reference density rho0 (rho0 < 0 asks for whole storage)");
   I->shape = default_shape(lattice, grid->prec);
   I->graph_steps = 64;
   I->graph_shape = -1;

@@ -141,30 +141,48 @@ extern "C" int lbm_conserved_noalloc(int lattice, int prec, double gamma, double
   double delta = 2.0 / (gamma - 1.0) - D;
   if (delta < -1e-12) return set_error(LBM_EINVAL, "gamma gives delta < 0 (gamma must be <= (D+2)/D)");
   if (delta < 0.0) delta = 0.0;
-  if (rho0 <= 0.0) rho0 = 1.0;
-  if (T0 <= 0.0) T0 = 1.0;
+  // the reference state as lbm_create resolves it
+  if (resolve_reference(prec, rho0, T0, &rho0, &T0) != LBM_OK)
+    return set_error(LBM_EINVAL, "16-bit storage needs a positive reference density rho0");
   if (ncells < 0) return set_error(LBM_EINVAL, "ncells must be >= 0");
   if (ncells > kNaMaxCells)
     return set_error(LBM_EINVAL, "ncells exceeds the no-allocation maximum of 16777216 cells "
                                  "(4096 blocks of 4096 cells of static scratch); use lbm_conserved");
   if (plane_stride < ncells) return set_error(LBM_EINVAL, "plane_stride must be >= ncells");
   if (ncells > 0 && !state) return set_error(LBM_EINVAL, "state is NULL");
+  if (ncells > 0) {
+    // the kernels read whole storage words (8 bytes FP64, 4 bytes FP32 and
+    // 16-bit pairs) from GPU memory of the current device: reject anything
+    // else here instead of faulting on the GPU
+    const size_t word = (prec == kF64) ? 8 : 4;
+    if (reinterpret_cast<uintptr_t>(state) % word != 0)
+      return set_error(LBM_EINVAL, "state is not aligned to its " + std::to_string(word) + "-byte storage word");
+    cudaPointerAttributes pa;
+    cudaError_t e = cudaPointerGetAttributes(&pa, state);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // clear the error this query may leave
+      return set_error(LBM_EINVAL, std::string("state is not a CUDA pointer: ") + cudaGetErrorString(e));
+    }
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+      return set_error(LBM_EINVAL, "state must be device or managed memory");
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(LBM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (pa.type == cudaMemoryTypeDevice && pa.device != dev)
+      return set_error(LBM_EINVAL, "state lives on device " + std::to_string(pa.device) + ", not on the current device " +
+                                       std::to_string(dev));
+  }
 
   LatticeTable t;
   if (build_lattice_table(lattice, &t) != 0) return set_error(LBM_EINVAL, "lattice table refinement failed");
-  // 16-bit codec constants of the reference equilibrium (rho0, u = 0, T0)
+  // 16-bit codec constants of the reference equilibrium (rho0, u = 0, T0),
+  // from the same helper the instances use
   Args<float> af{};
-  const double th = T0 - 1.0;
+  double gref[10], pref[10], hscale[10];
+  reference_constants(t, delta, rho0, T0, gref, pref, hscale);
   for (int g = 0; g < 10; ++g) {
-    double gref = 1.0, hscale = 1.0;
-    if (g < t.G) {
-      const double x2 = t.x2g[g];
-      const double pref = 0.5 * th * (x2 - D) + 0.125 * th * th * (x2 * x2 - 2.0 * (D + 2.0) * x2 + D * (D + 2.0));
-      gref = t.wg[g] * rho0 * (1.0 + pref);
-      hscale = (delta > 0.0) ? 0.5 * delta * T0 * gref : gref;
-    }
-    af.gref[g] = (float)gref;
-    af.hscale[g] = (float)hscale;
+    af.gref[g] = (float)gref[g];
+    af.hscale[g] = (float)hscale[g];
   }
 
   double tmp[kRedVals] = {0.0, 0.0, 0.0, 0.0, 0.0};

@@ -98,6 +98,18 @@ int set_error(int code, const std::string& msg);
 int prepare_instance(Instance* I, int lattice, double gamma, double tau_f, double tau_g, const lbm_grid* grid);
 // Fills I->ad and I->af from the instance (after its flag pointer is set).
 void fill_instance_args(Instance* I);
+// The reference state an instance of precision prec stores its populations
+// against, from the caller's (rho0, T0): rho0 > 0 is taken as given; rho0 < 0
+// asks for whole storage (*rho0_out = 0, FP64 and FP32 storage only); 0 or
+// NaN is the precision's default, whole storage for FP64 and rho0 = 1 for
+// FP32 and 16-bit storage.  T0 that is not positive (NaN included) is 1.
+// Returns LBM_OK or LBM_EINVAL (whole storage asked for 16-bit storage).
+int resolve_reference(int prec, double rho0, double T0, double* rho0_out, double* T0_out);
+// Reference equilibrium per velocity group at (rho0, u = 0, T0), Eq. (18):
+// gref[g], pref[g] = gref / (w rho0) - 1, and the scale hscale[g] of the
+// 16-bit h codec (groups past t.G get 1, 0, 1).
+void reference_constants(const LatticeTable& t, double delta, double rho0, double T0, double* gref,
+                         double* pref, double* hscale);
 // Bytes of one population buffer (2Q planes, 256-byte rounded).
 size_t instance_buffer_bytes(int Q, long long N, int prec);
 const Launchers& launchers_for(int lattice, int prec);

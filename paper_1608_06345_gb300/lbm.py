@@ -282,8 +282,20 @@ def lbm_autotune(h, reps=5):
 
 def lbm_conserved_noalloc(lattice, prec, gamma, state, ncells, plane_stride, stream=None, rho0=0.0, T0=0.0):
     """Totals of a raw device state without any allocation (see include/lbm.h).
-    `state` is a device pointer (int) or a CUDA tensor; returns out[D + 2]."""
-    ptr = state if isinstance(state, int) else _ptr(state)
+    `state` is a device pointer (int) or a CUDA tensor; returns out[D + 2].
+    A tensor must hold the whole extent of the planes: (2Q-1) plane_stride +
+    ncells words (Q-1 strides plus ncells 4-byte pairs for 16-bit storage)."""
+    if isinstance(state, int):
+        ptr = state
+    else:
+        Q = 37 if lattice == LBM_D2Q37 else 107
+        word = 8 if prec == LBM_F64 else 4
+        planes = Q if prec in (LBM_F32_S16F, LBM_F32_S16BF) else 2 * Q
+        need = ((planes - 1) * int(plane_stride) + int(ncells)) * word if ncells > 0 else 0
+        have = state.numel() * state.element_size()
+        if have < need:
+            raise LbmError(LBM_EINVAL, f"state holds {have} bytes, the planes need {need}")
+        ptr = _ptr(state)
     out = np.zeros(2 + dim(lattice))
     _check(load().lbm_conserved_noalloc(lattice, prec, gamma, rho0, T0, ptr, int(ncells), int(plane_stride),
                                         stream, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
