@@ -463,12 +463,106 @@ def run_ours(args, wl):
                             "hbm_frac": hbm["frac"], "shape": hbm["shape"]}
     if wl["fields"] == "sod":
         line["us_per_lattice_step"] = elapsed / (args.steps * S) * 1e6
+    if world == 1 and args.workload == "periodic2d" and not args.no_configs:
+        line["configs"] = {name: measure_config(name, n) for name, n in CONFIG_RUNS}
     if world == 1 and args.workload == "periodic2d" and not args.no_serving:
         line["serving"] = serving_eval(args)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# The other workloads of the benchmark set, measured in the default run (one
+# GPU) so that each has a figure of its own: name -> (workload, lattice steps
+# timed).  Each timed region lasts about a second, so that the clock sampler
+# sees it; every state but the Sod tube's is far larger than L2.
+CONFIG_RUNS = [
+    ("periodic3d", 200),        # D3Q107 FP32 256^3, gamma 1.4
+    ("periodic3d_g13", 200),    # gamma 1.3
+    ("periodic3d_s16f", 400),   # D3Q107 FP16 storage 256^3
+    ("periodic2d_s16f", 1400),  # D2Q37 FP16 storage 4096^2
+    ("periodic2d_s16bf", 1400), # D2Q37 BF16 storage 4096^2
+    ("periodic2d_f64", 60),     # D2Q37 FP64 4096^2 (FP64-pipe bound)
+    ("fd2d", 400),              # finite-difference variant 4096^2
+    ("sod2d", 100000),          # D2Q37 FP64 Sod 1000x4 (latency bound)
+]
+
+
+def roofline_of(wl, N, step_s):
+    """Roofline record of one step: HBM bytes per cell update 2 Q 2 word
+    against the measured copy bandwidth, or for FP64 the flops per cell
+    update against the FP64 pipe."""
+    word = {"f64": 8, "f32": 4, "f32_s16f": 2, "f32_s16bf": 2}[wl["prec"]]
+    Q = 37 if wl["lattice"] == 0 else 107
+    bpc = 2 * Q * 2 * word
+    peak, peak_kind = measured_peaks()
+    hbm = N * bpc / step_s / 1e9
+    rec = {"bound": "hbm", "achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak,
+           "bytes_per_cell_update": bpc, "peak_kind": peak_kind}
+    if wl["prec"] == "f64" and wl.get("scheme") != "fd":
+        fl = FP64_FLOPS_PER_CELL[wl["lattice"]]
+        ach = fl * N / step_s / 1e9
+        rec = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+               "frac": ach / FP64_PEAK_GFLOPS, "flops_per_cell_update": fl,
+               "peak_kind": "derived: 152 SMs x 2 FP64 inst/clk x 2 flop x 2.07 GHz",
+               "hbm_achieved_gbs": hbm, "hbm_frac": hbm / peak}
+    return rec
+
+
+def measure_config(name, lattice_steps):
+    """One workload of CONFIG_RUNS on its own instance: autotuned shape, 3
+    warm-up lattice steps, then `lattice_steps` steps timed with CUDA events
+    on the instance's stream and the SM clocks sampled meanwhile."""
+    import torch
+
+    from paper_1608_06345_gb300 import autotune, lbm
+    wl = WORKLOADS[name]
+    shape = wl["shape"]
+    N = int(np.prod(shape))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rho, u, T = (torch.from_numpy(np.ascontiguousarray(f)).to(dev) for f in make_fields(wl, shape))
+    stream = torch.cuda.current_stream()
+    solver = lbm.Solver(wl["lattice"], wl["gamma"], wl["tau_f"], wl["tau_g"], shape, bc=wl.get("bc", (0, 0, 0)),
+                        prec=lbm.PREC_NAMES[wl["prec"]], stream=stream)
+    solver.init(rho, u, T)
+    fd = wl.get("scheme") == "fd"
+    tuned = {"index": -1} if fd else autotune.tune(solver, reps=3, cache_path=None)
+    step = (lambda n: solver.step_fd(n, wl["lam"])) if fd else solver.step
+    # whole solves of the workload's length: the Sod tube and the FD variant
+    # stay within the steps where they are defined
+    per = min(lattice_steps, wl["steps"])
+    step(3)
+    solver.sync()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    total, elapsed = 0, 0.0
+    while total < lattice_steps:
+        solver.init(rho, u, T)  # each timed run is one solve from the initial fields
+        torch.cuda.synchronize()
+        a.record(stream)
+        step(per)
+        b.record(stream)
+        b.synchronize()
+        elapsed += a.elapsed_time(b) / 1e3
+        total += per
+    clk = clocks.stop()
+    solver.sync()  # raises on a non-finite state
+    solver.close()
+    del rho, u, T
+    torch.cuda.empty_cache()
+    step_s = elapsed / total
+    rec = {"workload": wl["desc"], "lattice_steps_timed": total, "mlups": N / step_s / 1e6,
+           "step_kernel_us": step_s * 1e6, "roofline": roofline_of(wl, N, step_s), "clocks": clk,
+           "shape": {k: tuned.get(k) for k in ("index", "stage", "block")}}
+    if wl["fields"] == "sod":
+        rec["l2"] = "state 2.4 MB fits in L2: a latency-bound case, time per step is its figure"
+        rec["us_per_lattice_step"] = step_s * 1e6
+    return rec
 
 
 # ---------------------------------------------------------------------------
@@ -495,7 +589,8 @@ def serving_eval(args):
     serving.serve(reqs[:8], np.zeros(8), serving.PoolBackend(warm))
     warm.close()
 
-    cap = serving.summarize(batched(np.zeros(len(reqs))))
+    cap_recs = batched(np.zeros(len(reqs)))
+    cap = serving.summarize(cap_recs)
     capacity = cap["solves_per_s"]
     loads = []
     for f in (0.5, 0.8, 1.0):
@@ -505,16 +600,24 @@ def serving_eval(args):
         s["rate_per_s"] = f * capacity
         loads.append(s)
 
-    def make_solver(req):
-        s = lbm.Solver(0, req.gamma, req.tau_f, req.tau_g, req.shape, bc=req.bc, prec=lbm.LBM_F64)
+    def make_solver(req, prec=lbm.LBM_F64):
+        # FP64: whole storage (its default); FP32: the request's reference
+        # state, as in the pool, so that the FP32 arms differ in batching only
+        ref = dict(rho0=req.rho0, T0=req.T0) if prec == lbm.LBM_F32 else {}
+        s = lbm.Solver(0, req.gamma, req.tau_f, req.tau_g, req.shape, bc=req.bc, prec=prec, **ref)
         lbm.lbm_set_graph_steps(s.h, 0)  # the plain method: one launch per step
         return s
 
-    base = None
+    base = base32 = nonfinite = None
     if not args.no_baseline:
         arr = li.poisson_arrivals(len(reqs), rate=0.8 * capacity, seed=7)
-        base = serving.summarize(serving.serve_baseline(reqs, arr, make_solver))
+        b64_recs = serving.serve_baseline(reqs, arr, make_solver)
+        base = serving.summarize(b64_recs)
         base["offered_load_of_batched_capacity"] = 0.8
+        b32_recs = serving.serve_baseline(reqs, arr, lambda r: make_solver(r, lbm.LBM_F32))
+        base32 = serving.summarize(b32_recs)
+        base32["offered_load_of_batched_capacity"] = 0.8
+        nonfinite = nonfinite_breakdown(reqs, params, cap_recs, b32_recs, b64_recs, make_solver)
     cells_steps = sum(r.cells * r.steps for r in reqs)
     return {
         "workload": f"{len(reqs)} shock-tube solves, D2Q37 FP32, Nx log-uniform [256, 16384] x 4, gamma "
@@ -522,11 +625,72 @@ def serving_eval(args):
                     f"{args.serving_budget_mb} MB, bundle {args.bundle_steps} steps",
         "batched_solves_per_s": capacity, "capacity": cap, "poisson": loads,
         "baseline_fp64_one_per_launch": base,
+        "baseline_fp32_one_per_launch": base32,
         "p99_ms_at_0.8": loads[1]["p99_ms"],
         "baseline_p99_ms_at_0.8": base["p99_ms"] if base else None,
         "throughput_vs_baseline": capacity / base["solves_per_s"] if base else None,
+        "throughput_vs_fp32_baseline": capacity / base32["solves_per_s"] if base32 else None,
+        "nonfinite": nonfinite,
         "cell_updates_requested": cells_steps,
     }
+
+
+def first_nonfinite_step(req, solver, chunk=10):
+    """Lattice step (to `chunk` steps) at which an instance of the request
+    first meets a non-finite density or temperature, run alone; None if it
+    stays finite."""
+    from paper_1608_06345_gb300 import lbm
+    solver.init(*req.fields)
+    done = 0
+    try:
+        while done < req.steps:
+            n = min(chunk, req.steps - done)
+            solver.step(n)
+            done += n
+            solver.sync()
+    except lbm.LbmError as ex:
+        if ex.code != lbm.LBM_ENONFINITE:
+            raise
+        return done
+    finally:
+        solver.close()
+    return None
+
+
+def nonfinite_breakdown(reqs, params, pool_recs, b32_recs, b64_recs, make_solver):
+    """Which requests go non-finite in which arm.  The pooled FP32 instance
+    computes bitwise what the same instance computes alone, so the pool and
+    the plain FP32 arm must agree request by request.  Requests non-finite
+    in FP32 but finite in FP64 are listed with their parameters and the step
+    at which the FP32 run first meets a non-finite state (run alone, to 10
+    steps); the pool itself stops such an instance at the step where its
+    error word is set and reports it at the end of that bundle."""
+    from paper_1608_06345_gb300 import lbm
+    bad = lambda recs: {r.rid for r in recs if r.status == "nonfinite"}
+    p32, s32, s64 = bad(pool_recs), bad(b32_recs), bad(b64_recs)
+    by_id = {p["id"]: p for p in params}
+    only32 = []
+    for req in reqs:
+        if req.rid in p32 and req.rid not in s64:
+            p = by_id[req.rid]
+            only32.append({"id": req.rid, "nx": p["nx"], "gamma": p["gamma"], "tau": p["tau"], "steps": p["steps"],
+                           "rho_ratio": p["left"][0] / p["right"][0],
+                           "p_ratio": (p["left"][0] * p["left"][2]) / (p["right"][0] * p["right"][2]),
+                           "fp32_nonfinite_at_step": first_nonfinite_step(req, make_solver(req, lbm.LBM_F32))})
+    # step at which each pooled FP32 failure first meets a non-finite state
+    # (run alone, to 10 steps): the device stops the instance there and the
+    # host reports it at the end of that bundle, at most bundle_steps later
+    pairs = [(first_nonfinite_step(req, make_solver(req, lbm.LBM_F32)), req.steps) for req in reqs
+             if req.rid in p32]
+    at = [a for a, _ in pairs if a is not None]
+    steps = [n for a, n in pairs if a is not None]
+    return {"pool_fp32": len(p32), "plain_fp32": len(s32), "plain_fp64": len(s64),
+            "pool_equals_plain_fp32": p32 == s32, "fp32_only": only32, "fp64_only": sorted(s64 - p32),
+            "fp32_nonfinite_at_step": {"min": min(at) if at else None,
+                                       "median": float(np.median(at)) if at else None,
+                                       "max": max(at) if at else None,
+                                       "median_fraction_of_requested_steps":
+                                           float(np.median(np.array(at) / np.array(steps))) if at else None}}
 
 
 def run_serving(args):
@@ -559,6 +723,7 @@ def main():
     ap.add_argument("--bundle-steps", type=int, default=50)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving summary of the default line")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads of the default line")
     args = ap.parse_args()
     if args.workload == "serving":
         run_serving(args)
