@@ -319,7 +319,56 @@ int lbm_pool_result(lbm_pool_handle p, long long ticket, double* rho, double* u,
  * use, arena bytes, work-list entries, persistent grid blocks. */
 int lbm_pool_stats(lbm_pool_handle p, long long* out);
 
-/* General Hermite quadrature (the construction of Sec. IV, for any
+/* ------------------------------------------------------------------------
+ * Slab decomposition of one grid along its slowest axis (y for D2Q37, z for
+ * D3Q107) over nranks ranks: host-side plan, pack and unpack.  The paper
+ * has no parallel design; this is the halo exchange a multi-GPU run of the
+ * step would use.  A step pulls from at most 3 cells away per axis
+ * (|c_a| <= 3 in Tables I/II), so a slab with 3 ghost layers on each side,
+ * refreshed before every step, steps its owned cells exactly as the whole
+ * grid would: ghost layer begin - k (k = 1..3) is read only by the
+ * velocities with c_axis >= k, ghost layer end + k - 1 only by those with
+ * c_axis <= -k, and only those populations travel.  At a zero-gradient end
+ * the ghost layers repeat the edge layer (the clamped pull).
+ * These calls work on host arrays in the raw FP64 layout of lbm_get_state
+ * (2Q planes of plane_stride values: g for velocities 0..Q-1 in the order of
+ * lbm_lattice_table, then h; cell x + nx (y + ny z) of the rank's local
+ * grid local_n, its owned layers plus 3 ghost layers per side).  Every box
+ * of this build has one GPU, so no device transport is provided; a rank
+ * steps its local grid with the split axis' boundary set to zero-gradient.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int lattice, axis;      /* lattice; split axis (1 = y for D2Q37, 2 = z for D3Q107) */
+  int n[3];               /* global grid */
+  int periodic;           /* 1: periodic split axis, 0: zero-gradient ends */
+  int nranks, rank;
+  int begin, end;         /* owned global layers [begin, end) along the axis */
+  int lo, hi;             /* neighbour ranks below / above; -1 at a zero-gradient end */
+  int layer_cells;        /* cells per layer (nx in 2D, nx ny in 3D) */
+  int local_n[3];         /* local grid: n with end - begin + 6 layers along the axis;
+                             local layer k is global layer begin - 3 + k */
+  long long msg_values;   /* doubles in each message (either direction) */
+} lbm_slab;
+
+/* Plan of rank `rank`: layers split as evenly as possible (rank r owns
+ * [L r / nranks, L (r+1) / nranks)).  LBM_EINVAL for a bad lattice, grid or
+ * rank, or a slab thinner than 3 layers. */
+int lbm_slab_plan(int lattice, const int n[3], int periodic, int nranks, int rank, lbm_slab* out);
+
+/* Pack the two messages of msg_values doubles: to_hi (for the rank above)
+ * holds, for k = 1..3, owned layer end - k of every population with
+ * c_axis >= k (g planes, then h); to_lo (for the rank below) owned layer
+ * begin + k - 1 of those with c_axis <= -k.  Either output may be NULL. */
+int lbm_slab_pack(const lbm_slab* s, const double* state, long long plane_stride, double* to_lo, double* to_hi);
+
+/* Unpack the neighbours' messages into the ghost layers: from_lo (the rank
+ * below's to_hi) and from_hi (the rank above's to_lo); at a zero-gradient
+ * end the ghost layers get copies of the edge layer (every plane) and the
+ * message pointer of that side may be NULL. */
+int lbm_slab_unpack(const lbm_slab* s, double* state, long long plane_stride, const double* from_lo,
+                    const double* from_hi);
+
+/* General Hermite quadrature (the construction of Sec. IV, for any/* General Hermite quadrature (the construction of Sec. IV, for any
  * symmetric integer velocity set): the velocities are all sign flips and
  * axis permutations of the ngroups representatives reps[ngroups*D]
  * (D = 1..3); find one weight per group w_group[ngroups] and the scale r

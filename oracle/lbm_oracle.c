@@ -711,13 +711,26 @@ void ora_moments(const ora_state* s, double* rho, double* u, double* T) {
   }
 }
 
+/* Neumaier's compensated summation (Neumaier 1974): the running sum s and
+ * the accumulated rounding error c of its additions; the total is s + c. */
+typedef struct { double s, c; } ksum_t;
+
+static void ksum_add(ksum_t* k, double v) {
+  const double t = k->s + v;
+  if (fabs(k->s) >= fabs(v)) k->c += (k->s - t) + v;
+  else k->c += (v - t) + k->s;
+  k->s = t;
+}
+
 /* Grid totals of the stored state: out = [mass, momentum[D], energy] with
- * mass = sum g, momentum = sum xi g, energy = sum (xi^2/2 g + h).  Plain
- * sequential summation. */
+ * mass = sum g, momentum = sum xi g, energy = sum (xi^2/2 g + h), Eq. (14).
+ * Summed in cell order with compensated sums: a plain running sum over the
+ * Q N terms of a grid drifts by up to ~1e-12 relative (measured on a 1024-cell
+ * D3Q107 tube), more than the round-off the conservation pins resolve. */
 void ora_conserved(const ora_state* s, double* out) {
   const long N = s->N;
   const int Q = s->L.Q, D = s->L.D;
-  double m = 0.0, j[3] = {0.0, 0.0, 0.0}, e = 0.0;
+  ksum_t m = {0.0, 0.0}, j[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}}, e = {0.0, 0.0};
   for (long cell = 0; cell < N; ++cell)
     for (int i = 0; i < Q; ++i) {
       double gi = s->g[i * N + cell], hi = s->h[i * N + cell];
@@ -728,15 +741,15 @@ void ora_conserved(const ora_state* s, double* out) {
       double x2 = 0.0;
       for (int a = 0; a < D; ++a) {
         double xi = s->L.r * s->L.c[i][a];
-        j[a] += xi * gi;
+        ksum_add(&j[a], xi * gi);
         x2 += xi * xi;
       }
-      m += gi;
-      e += 0.5 * x2 * gi + hi;
+      ksum_add(&m, gi);
+      ksum_add(&e, 0.5 * x2 * gi + hi);
     }
-  out[0] = m;
-  for (int a = 0; a < D; ++a) out[1 + a] = j[a];
-  out[1 + D] = e;
+  out[0] = m.s + m.c;
+  for (int a = 0; a < D; ++a) out[1 + a] = j[a].s + j[a].c;
+  out[1 + D] = e.s + e.c;
 }
 
 /* Direct access to the populations, [i * N + cell], in the oracle's own

@@ -18,7 +18,8 @@ LIB = os.path.join(OUT_DIR, "liblbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 # (source, extra defines): step_inst.cu is built once per (lattice, precision)
-SOURCES = [("lbm_api.cu", []), ("lattice_table.cpp", []), ("lbm_noalloc.cu", []), ("lbm_pool.cu", [])] + [
+SOURCES = [("lbm_api.cu", []), ("lattice_table.cpp", []), ("lbm_slab.cpp", []), ("lbm_noalloc.cu", []),
+           ("lbm_pool.cu", [])] + [
     ("step_inst.cu", [f"-DLBM_LAT={lat}", f"-DLBM_PREC={prec}"]) for lat in (0, 1) for prec in (0, 1, 2, 3)]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -34,7 +34,8 @@ EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init
            "lbm_conserved_noalloc", "lbm_pool_bytes", "lbm_pool_create", "lbm_pool_destroy",
            "lbm_pool_instance_bytes", "lbm_pool_submit", "lbm_pool_run", "lbm_pool_sync", "lbm_pool_poll",
            "lbm_pool_result", "lbm_pool_stats", "lbm_shape_info", "lbm_set_shape", "lbm_get_shape",
-           "lbm_autotune", "lbm_set_graph_steps", "lbm_quadrature", "lbm_step_fd"]
+           "lbm_autotune", "lbm_set_graph_steps", "lbm_quadrature", "lbm_step_fd", "lbm_slab_plan",
+           "lbm_slab_pack", "lbm_slab_unpack"]
 
 
 class LbmError(RuntimeError):
@@ -48,6 +49,13 @@ class lbm_grid(ctypes.Structure):
                 ("bc", ctypes.c_int * 3), ("prec", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("device_mem", ctypes.c_void_p), ("device_bytes", ctypes.c_size_t),
                 ("rho0", ctypes.c_double), ("T0", ctypes.c_double)]
+
+
+class lbm_slab(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("axis", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("periodic", ctypes.c_int), ("nranks", ctypes.c_int), ("rank", ctypes.c_int),
+                ("begin", ctypes.c_int), ("end", ctypes.c_int), ("lo", ctypes.c_int), ("hi", ctypes.c_int),
+                ("layer_cells", ctypes.c_int), ("local_n", ctypes.c_int * 3), ("msg_values", ctypes.c_longlong)]
 
 
 class lbm_pool_config(ctypes.Structure):
@@ -105,6 +113,10 @@ def load(build_if_missing: bool = False):
         "lbm_set_graph_steps": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_quadrature": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ip, ctypes.c_double, ip,
                                           dp, dp, dp]),
+        "lbm_slab_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.POINTER(lbm_slab)]),
+        "lbm_slab_pack": (ctypes.c_int, [ctypes.POINTER(lbm_slab), vp, ctypes.c_longlong, vp, vp]),
+        "lbm_slab_unpack": (ctypes.c_int, [ctypes.POINTER(lbm_slab), vp, ctypes.c_longlong, vp, vp]),
         "lbm_pool_bytes": (ctypes.c_size_t, [ctypes.POINTER(lbm_pool_config)]),
         "lbm_pool_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(lbm_pool_config)]),
         "lbm_pool_destroy": (ctypes.c_int, [vp]),
@@ -300,6 +312,30 @@ def lbm_conserved_noalloc(lattice, prec, gamma, state, ncells, plane_stride, str
     _check(load().lbm_conserved_noalloc(lattice, prec, gamma, rho0, T0, ptr, int(ncells), int(plane_stride),
                                         stream, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def lbm_slab_plan(lattice, n, periodic, nranks, rank):
+    """Slab plan of one rank (include/lbm.h); returns an lbm_slab."""
+    nn = (ctypes.c_int * 3)(*[int(v) for v in tuple(n) + (1,) * (3 - len(n))])
+    s = lbm_slab()
+    _check(load().lbm_slab_plan(lattice, nn, int(bool(periodic)), nranks, rank, ctypes.byref(s)))
+    return s
+
+
+def lbm_slab_pack(s, state, plane_stride, to_lo, to_hi):
+    """state: float64 array of 2Q planes of plane_stride values; to_lo /
+    to_hi: float64 arrays of s.msg_values (or None)."""
+    for a in (to_lo, to_hi):
+        assert a is None or (a.dtype == np.float64 and a.size >= s.msg_values)
+    assert state.dtype == np.float64 and state.flags.c_contiguous
+    _check(load().lbm_slab_pack(ctypes.byref(s), _ptr(state), int(plane_stride), _ptr(to_lo), _ptr(to_hi)))
+
+
+def lbm_slab_unpack(s, state, plane_stride, from_lo, from_hi):
+    for a in (from_lo, from_hi):
+        assert a is None or (a.dtype == np.float64 and a.size >= s.msg_values)
+    assert state.dtype == np.float64 and state.flags.c_contiguous
+    _check(load().lbm_slab_unpack(ctypes.byref(s), _ptr(state), int(plane_stride), _ptr(from_lo), _ptr(from_hi)))
 
 
 def lbm_last_error():

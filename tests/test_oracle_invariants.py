@@ -191,3 +191,22 @@ def test_shear_wave_viscous_decay(lat, D, tau):
     nu = (tau - 0.5) * 1.0 / r ** 2
     expected = A * np.exp(-nu * (2 * np.pi / nx) ** 2 * steps)
     assert abs(amp / expected - 1.0) < 5e-3, (amp / A, expected / A)
+
+
+@pytest.mark.parametrize("lat,shape", [(ora.D2Q37, (300, 7)), (ora.D3Q107, (64, 3, 2))])
+def test_totals_are_the_exact_sums(lat, shape):
+    """ora_conserved's compensated sums equal the exactly rounded sums
+    (math.fsum) of mass, momentum and energy over every population of the
+    grid, Eq. (14), to a few ulps."""
+    import math
+    D = len(shape)
+    N = int(np.prod(shape))
+    s = run(lat, 1.4, 0.6, 0.7, shape, li.random_fields(N, D, seed=21), 7)
+    c = s.conserved()
+    g, h = s.get_pops()
+    cv, w, r = ora.lattice_info(lat)
+    xi = r * cv
+    exact = [math.fsum(g.ravel())] + [math.fsum((xi[:, a:a + 1] * g).ravel()) for a in range(D)] + \
+            [math.fsum((0.5 * (xi ** 2).sum(1)[:, None] * g + h).ravel())]
+    scale = np.array([abs(exact[0])] * (1 + D) + [abs(exact[-1])])
+    assert np.all(np.abs(c - np.array(exact)) <= 4 * 2.0 ** -53 * scale), (c, exact)
