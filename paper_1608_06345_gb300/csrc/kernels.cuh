@@ -774,81 +774,6 @@ __global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S*
 }
 
 // ---------------------------------------------------------------------------
-// persistent step with L2 prefetch (shape stage 9): a grid of resident
-// blocks walks the tiles (BX cells of a row) in order; before stepping tile
-// t a block asks L2 for the source data of its next tile, t + gridDim.x,
-// with one bulk prefetch per population plane (the pull of direction i for
-// a tile reads one contiguous row segment per plane: x0 - c_x .. x0 - c_x +
-// BX of row (y - c_y, z - c_z)).  The prefetches hold no register and no
-// shared memory, and by the time the block reaches that tile its loads
-// find the data in L2 instead of waiting for DRAM.  The step itself is
-// step_cell with the tile's staging (STAGE 3 or 6).
-// ---------------------------------------------------------------------------
-struct VelTable {
-  signed char c[107][3];
-};
-
-__host__ __device__ constexpr VelTable make_vel_table(const LatticeDef& L) {
-  VelTable t{};
-  for (int i = 0; i < L.Q; ++i)
-    for (int a = 0; a < 3; ++a) t.c[i][a] = (signed char)L.c[i][a];
-  return t;
-}
-
-// velocity components for runtime indexing in device code
-__device__ const VelTable kVelDev[2] = {make_vel_table(kD2Q37), make_vel_table(kD3Q107)};
-
-// source row segments of the tile (x0 .. x0 + BX - 1, y, z), one bulk L2
-// prefetch per plane; thread t takes directions t, t + BX, ...  Segments are
-// clipped to the row (a periodic wrap is left out) and rounded to 16 bytes
-// inside the row; nothing is prefetched outside the source buffer.
-template <int LAT, class S, class C, int BX>
-__device__ __forceinline__ void prefetch_tile_l2(const S* __restrict__ src, const Args<C>& a, int x0, int y,
-                                                 int z) {
-  constexpr int Q = Lat<LAT>::Q;
-  constexpr bool S16 = IsS16<S>::value;
-  constexpr long long E = S16 ? 2 * (long long)sizeof(S) : (long long)sizeof(S);  // bytes per element
-  constexpr long long PER = 16 / E;                                              // elements per 16 bytes
-  const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
-  const char* base = reinterpret_cast<const char*>(src);
-  for (int i = threadIdx.x; i < Q; i += BX) {
-    const signed char* c = kVelDev[LAT].c[i];
-    const long long ys = pull_coord(y, c[1], ny, a.bc[1]);
-    const long long zs = (Lat<LAT>::D == 3) ? pull_coord(z, c[2], nz, a.bc[2]) : 0;
-    const long long row = (long long)nx * (ys + (long long)ny * zs);
-    int xs0 = x0 - c[0], xs1 = x0 - c[0] + BX;
-    xs0 = xs0 < 0 ? 0 : xs0;
-    xs1 = xs1 > nx ? nx : xs1;
-    if (xs1 <= xs0) continue;
-#pragma unroll
-    for (int half = 0; half < (S16 ? 1 : 2); ++half) {
-      const long long pl = (long long)(i + half * Q) * a.ps + row;
-      const long long e0 = (pl + xs0) / PER * PER, e1 = (pl + xs1) / PER * PER;
-      if (e1 > e0)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(base + e0 * E),
-                     "r"((unsigned)((e1 - e0) * E))
-                     : "memory");
-    }
-  }
-}
-
-template <int LAT, class S, class C, int STAGE, int BX, int MINB, bool IDX32>
-__global__ void __launch_bounds__(BX, MINB) k_step_pf(const S* __restrict__ src, S* __restrict__ dst,
-                                                     const Args<C> a, int tiles_x, long long ntiles) {
-  const int ny = a.n[1];
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const long long tn = t + gridDim.x;
-    if (tn < ntiles) {
-      const long long r = tn / tiles_x;
-      prefetch_tile_l2<LAT, S, C, BX>(src, a, (int)(tn % tiles_x) * BX, (int)(r % ny), (int)(r / ny));
-    }
-    const long long r = t / tiles_x;
-    step_cell<LAT, S, C, STAGE, BX, IDX32>(src, dst, a, (int)(t % tiles_x) * BX + (int)threadIdx.x, (int)(r % ny),
-                                           (int)(r / ny));
-  }
-}
-
-// ---------------------------------------------------------------------------
 // the velocity-split step (STAGE 4): a block of P warps covers 32 cells of a
 // row; warp w pulls, sums and relaxes only its part [begin(w), end(w)) of the
 // velocities.  The parts' five partial sums meet in shared memory and every

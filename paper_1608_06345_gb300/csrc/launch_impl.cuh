@@ -72,48 +72,6 @@ cudaError_t launch_step_split(const Instance* inst, const void* src, void* dst, 
   return cudaGetLastError();
 }
 
-// the persistent prefetching step (stage 9): a grid of resident blocks
-// (SMs x blocks per SM, found once per device when the shape is configured)
-template <int LAT, class S, class C, int STAGE, int BX, int MINB, bool IDX32>
-cudaError_t launch_step_pf_v(const Instance* inst, const void* src, void* dst, const Args<C>& a,
-                             bool configure_only) {
-  auto kern = k_step_pf<LAT, S, C, STAGE, BX, MINB, IDX32>;
-  constexpr size_t smem = step_smem<LAT, S, STAGE, BX>();
-  static std::atomic<int> grid_of[64] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev >= 64) return cudaErrorInvalidDevice;
-  int g = grid_of[dev].load(std::memory_order_acquire);
-  if (g == 0) {
-    if (smem > 48 * 1024) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    int sms = 0, per_sm = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BX, smem);
-    if (e != cudaSuccess) return e;
-    g = sms * (per_sm > 0 ? per_sm : 1);
-    grid_of[dev].store(g, std::memory_order_release);
-  }
-  if (configure_only) return cudaSuccess;
-  const int tiles_x = (inst->n[0] + BX - 1) / BX;
-  const long long ntiles = (long long)tiles_x * inst->n[1] * inst->n[2];
-  const unsigned grid = (unsigned)(ntiles < g ? ntiles : g);
-  kern<<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst), a, tiles_x, ntiles);
-  return cudaGetLastError();
-}
-
-template <int LAT, class S, class C, int STAGE, int BX, int MINB>
-cudaError_t launch_step_pf(const Instance* inst, const void* src, void* dst, const Args<C>& a,
-                           bool configure_only = false) {
-  const long long planes = IsS16<S>::value ? Lat<LAT>::Q : 2LL * Lat<LAT>::Q;
-  if (planes * inst->ps < (1LL << 32))
-    return launch_step_pf_v<LAT, S, C, STAGE, BX, MINB, true>(inst, src, dst, a, configure_only);
-  return launch_step_pf_v<LAT, S, C, STAGE, BX, MINB, false>(inst, src, dst, a, configure_only);
-}
-
 // the mirror-pair step (stage 8): BX threads, BX / 2 cells per block; HS
 // stages h in shared memory (FP32/FP64 storage)
 template <int LAT, class S, class C, int BX, int MINB, bool HS, bool IDX32>
@@ -155,14 +113,13 @@ cudaError_t launch_step_mirror(const Instance* inst, const void* src, void* dst,
 //   D2Q37 FP32:        (0,128,4) (0,256,2) (0,64,8) (0,128,1)
 //   D2Q37 16-bit:      (6,128,8) (6,128,7) (6,128,6) (6,256,3) (0,128,4) (0,64,8)
 //   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)  (4,32,4)  (7,32,4)
-//   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)  (8,32,8)  (8,64,4)  (9,64,6)
+//   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)  (8,32,8)  (8,64,4)  (3,128,3)
 //   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)  (7,32,3)
-//   D3Q107 16-bit:     (6,64,6)  (2,64,8)  (2,64,1)  (4,32,6)  (8,32,10) (8,32,12) (9,64,6)
+//   D3Q107 16-bit:     (6,64,6)  (2,64,8)  (2,64,1)  (4,32,6)  (8,32,10) (8,32,12) (6,128,3)
 // Stage 4 is the velocity-split step: 4 warps per block of 32 cells; stage 7
 // the same with the per-cell coefficients formed once by warp 0 and shared.
 // Stage 8 is the mirror-pair step: two lanes per cell (c and -c of every
-// pair), h staged in shared memory for FP32.  Stage 9 is stage 3 (FP32) or
-// 6 (16-bit) run by persistent blocks that prefetch their next tile into L2.  The moments of stages 4, 7
+// pair), h staged in shared memory for FP32.  The moments of stages 4, 7
 // and 8 are summed in another order, so their results differ from the
 // other shapes' by rounding; the defaults (index 0) are the shapes the
 // batched pool uses, whose results are bitwise those of a lone instance.
@@ -174,9 +131,9 @@ struct StepShapes {
     static const int s2[4][3] = {{0, 128, 4}, {0, 256, 2}, {0, 64, 8}, {0, 128, 1}};
     static const int s2h[6][3] = {{6, 128, 8}, {6, 128, 7}, {6, 128, 6}, {6, 256, 3}, {0, 128, 4}, {0, 64, 8}};
     static const int s2d[5][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}, {4, 32, 4}, {7, 32, 4}};
-    static const int s3f[7][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}, {8, 32, 8}, {8, 64, 4}, {9, 64, 6}};
+    static const int s3f[7][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}, {8, 32, 8}, {8, 64, 4}, {3, 128, 3}};
     static const int s3d[4][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}, {7, 32, 3}};
-    static const int s3h[7][3] = {{6, 64, 6}, {2, 64, 8}, {2, 64, 1}, {4, 32, 6}, {8, 32, 10}, {8, 32, 12}, {9, 64, 6}};
+    static const int s3h[7][3] = {{6, 64, 6}, {2, 64, 8}, {2, 64, 1}, {4, 32, 6}, {8, 32, 10}, {8, 32, 12}, {6, 128, 3}};
     const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : (sizeof(S) == 2 ? s2h : s2))
                                   : (sizeof(S) == 4 ? s3f : (sizeof(S) == 8 ? s3d : s3h));
     *stage = t[k][0];
@@ -229,7 +186,7 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
       case 3: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
       case 4: return launch_step_mirror<LAT, S, C, 64, 8, true>(inst, src, dst, a, configure_only);
       case 5: return launch_step_mirror<LAT, S, C, 128, 4, true>(inst, src, dst, a, configure_only);
-      case 6: return launch_step_pf<LAT, S, C, 3, 64, 6>(inst, src, dst, a, configure_only);
+      case 6: return launch_step_t<LAT, S, C, 3, 128, 3>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 3, 64, 6>(inst, src, dst, a, configure_only);
     }
   } else if constexpr (sizeof(S) == 8) {
@@ -246,7 +203,7 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
       case 3: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
       case 4: return launch_step_mirror<LAT, S, C, 64, 10, false>(inst, src, dst, a, configure_only);
       case 5: return launch_step_mirror<LAT, S, C, 64, 12, false>(inst, src, dst, a, configure_only);
-      case 6: return launch_step_pf<LAT, S, C, 6, 64, 6>(inst, src, dst, a, configure_only);
+      case 6: return launch_step_t<LAT, S, C, 6, 128, 3>(inst, src, dst, a, configure_only);
       default: return launch_step_t<LAT, S, C, 6, 64, 6>(inst, src, dst, a, configure_only);
     }
   }
