@@ -351,8 +351,14 @@ def run_ours(args, wl):
     # only the idle buffer; the state is untouched)
     from paper_1608_06345_gb300 import autotune
     solver.init(d_rho, d_u, d_T)
-    tuned = autotune.tune(solver, reps=5, cache_path=None) if wl.get("scheme") != "fd" else \
-        {"index": -1, "stage": 0, "block": 128 if wl["lattice"] == 0 else 64}
+    if wl.get("scheme") == "fd":
+        tuned = {"index": -1, "stage": 0, "block": 128 if wl["lattice"] == 0 else 64}
+    elif args.shape is not None:  # a fixed compiled shape instead of the autotuner's pick (profiling)
+        lbm.lbm_set_shape(solver.h, args.shape)
+        st, bx = lbm.lbm_shape_info(wl["lattice"], prec, args.shape)
+        tuned = {"index": args.shape, "stage": st, "block": bx}
+    else:
+        tuned = autotune.tune(solver, reps=5, cache_path=None)
 
     for _ in range(max(args.warmup, 0)):
         bench_step()
@@ -556,8 +562,12 @@ def measure_config(name, lattice_steps):
     del rho, u, T
     torch.cuda.empty_cache()
     step_s = elapsed / total
+    roof = roofline_of(wl, N, step_s)
+    kname = "k_step_fd" if fd else "k_step"
+    roof["kernel"] = f"{kname}_{'d2q37' if wl['lattice'] == 0 else 'd3q107'}_{wl['prec']}_{'x'.join(map(str, shape))}"
+    roof["traffic"] = recorded_traffic(roof["kernel"])
     rec = {"workload": wl["desc"], "lattice_steps_timed": total, "mlups": N / step_s / 1e6,
-           "step_kernel_us": step_s * 1e6, "roofline": roofline_of(wl, N, step_s), "clocks": clk,
+           "step_kernel_us": step_s * 1e6, "roofline": roof, "clocks": clk,
            "shape": {k: tuned.get(k) for k in ("index", "stage", "block")}}
     if wl["fields"] == "sod":
         rec["l2"] = "state 2.4 MB fits in L2: a latency-bound case, time per step is its figure"
@@ -724,6 +734,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving summary of the default line")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads of the default line")
+    ap.add_argument("--shape", type=int, default=None,
+                    help="run this compiled step shape (lbm_shape_info index) instead of autotuning")
     args = ap.parse_args()
     if args.workload == "serving":
         run_serving(args)

@@ -612,26 +612,41 @@ __device__ __forceinline__ C raw_value(S v) {
 //            unpacked where each pass uses them
 // A block covers BX consecutive cells of a row (thread = cell).
 // ---------------------------------------------------------------------------
-template <int LAT, class S, class C, int STAGE, int BX, bool IDX32 = false>
+// ROW: the block's row (y, z) lies at least 3 cells from every y and z face,
+// so no pull of the row wraps or clamps along y or z: the source row of
+// direction i is the cell's own row shifted by -(c_y nx + c_z nx ny), the same
+// for every thread.  Only the x part of the pull differs between threads (a
+// 7-entry table of byte offsets); plane and row shifts are uniform, and the
+// stores address the cell through one per-thread pointer plus the uniform
+// plane stride.  The arithmetic is that of the general path.
+template <int LAT, class S, class C, int STAGE, int BX, bool IDX32 = false, bool ROW = false>
 __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restrict__ dst, const Args<C>& a, int x,
                                           int y, int z) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
   const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
   if (x >= nx) return;
-  // source offsets for lattice components c = -3..3 (index c + 3)
-  unsigned xo[7], yo[7], zo[7];
+  constexpr size_t E = IsS16<S>::value ? 2 * sizeof(S) : sizeof(S);  // bytes per stored element (pair)
+  // source offsets for lattice components c = -3..3 (index c + 3); ROW keeps
+  // only xb, the byte offset of the pulled x in the cell's own row
+  unsigned xo[ROW ? 1 : 7], yo[ROW ? 1 : 7], zo[ROW ? 1 : 7], xb[ROW ? 7 : 1];
+  const unsigned rowcell = (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    xo[k] = (unsigned)pull_coord(x, k - 3, nx, a.bc[0]);
-    yo[k] = (unsigned)pull_coord(y, k - 3, ny, a.bc[1]) * (unsigned)nx;
-    zo[k] = (L::D == 3) ? (unsigned)pull_coord(z, k - 3, nz, a.bc[2]) * (unsigned)nx * (unsigned)ny : 0u;
+    if constexpr (ROW) {  // element index of the pulled x in the cell's own row (a byte offset without IDX32)
+      xb[k] = (rowcell + (unsigned)pull_coord(x, k - 3, nx, a.bc[0])) * (IDX32 ? 1u : (unsigned)E);
+    } else {
+      xo[k] = (unsigned)pull_coord(x, k - 3, nx, a.bc[0]);
+      yo[k] = (unsigned)pull_coord(y, k - 3, ny, a.bc[1]) * (unsigned)nx;
+      zo[k] = (L::D == 3) ? (unsigned)pull_coord(z, k - 3, nz, a.bc[2]) * (unsigned)nx * (unsigned)ny : 0u;
+    }
   }
-  const unsigned cell = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+  const unsigned cell = (unsigned)x + rowcell;
   const long long ps = a.ps;
   auto src_off = [&](auto I) -> unsigned {
     constexpr int i = decltype(I)::value;
-    return zo[L::cz(i) + 3] + yo[L::cy(i) + 3] + xo[L::cx(i) + 3];
+    if constexpr (ROW) return 0u;  // not used on the ROW path
+    else return zo[L::cz(i) + 3] + yo[L::cy(i) + 3] + xo[L::cx(i) + 3];
   };
   // addresses = plane base (uniform across the grid) + per-thread byte
   // offset; g_i and h_i share the offset of direction i
@@ -645,17 +660,38 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
   // element index of the buffer is below 2^32 -- in unsigned 32-bit element
   // arithmetic, else plane base + 64-bit byte offset
   auto pptr = [&](int plane, auto I) -> const char* {
-    constexpr size_t E = IsS16<S>::value ? 2 * sizeof(S) : sizeof(S);
-    if constexpr (IDX32)
+    constexpr int i = decltype(I)::value;
+    if constexpr (ROW && IDX32) {
+      // uniform part plane ps - c_y nx - c_z nx ny plus the thread's x index,
+      // in unsigned 32-bit arithmetic: the sum is the element index, below 2^32
+      const unsigned u = (unsigned)plane * (unsigned)ps - (unsigned)(L::cy(i) * nx) -
+                         (unsigned)(L::cz(i)) * ((unsigned)nx * (unsigned)ny);
+      return reinterpret_cast<const char*>(src) + (size_t)(u + xb[L::cx(i) + 3]) * E;
+    } else if constexpr (ROW) {
+      const long long shift = -((long long)L::cy(i) * nx + (long long)L::cz(i) * nx * ny) * (long long)E;
+      return sb + ((long long)plane * ps * (long long)E + shift) + xb[L::cx(i) + 3];
+    } else if constexpr (IDX32) {
       return reinterpret_cast<const char*>(src) + (size_t)((unsigned)plane * (unsigned)ps + src_off(I)) * E;
-    else
+    } else {
       return sb + (size_t)plane * ((size_t)ps * E) + (size_t)src_off(I) * E;
+    }
   };
+  constexpr bool SIDX32 = IDX32;
   if constexpr (STAGE == 0) {
     C g[Q], h[Q];
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      if constexpr (IsS16<S>::value) {  // one 32-bit pair holds g_i and h_i
+      if constexpr (ROW) {
+        if constexpr (IsS16<S>::value) {
+          float lo, hi;
+          unpack16<S>(__ldg(reinterpret_cast<const unsigned*>(pptr(i, I))), lo, hi);
+          g[i] = lo;
+          h[i] = hi;
+        } else {
+          g[i] = raw_value<S, C>(ldg_s(reinterpret_cast<const S*>(pptr(i, I))));
+          h[i] = raw_value<S, C>(ldg_s(reinterpret_cast<const S*>(pptr(Q + i, I))));
+        }
+      } else if constexpr (IsS16<S>::value) {  // one 32-bit pair holds g_i and h_i
         const unsigned* sp = reinterpret_cast<const unsigned*>(src);
         const unsigned v = IDX32 ? __ldg(sp + ((unsigned)i * (unsigned)ps + src_off(I)))
                                  : __ldg(sp + ((size_t)i * ps + src_off(I)));
@@ -673,8 +709,8 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
         h[i] = raw_value<S, C>(ld(I, Q + i, offb));
       }
     });
-    collide_store<LAT, S, C, IDX32>([&](auto I) { return g[decltype(I)::value]; },
-                             [&](auto I) { return h[decltype(I)::value]; }, a, dst, ps, cell);
+    collide_store<LAT, S, C, SIDX32>([&](auto I) { return g[decltype(I)::value]; },
+                                     [&](auto I) { return h[decltype(I)::value]; }, a, dst, ps, cell);
   } else if constexpr (STAGE == 6) {
     static_assert(IsS16<S>::value, "packed pairs need 16-bit storage");
     unsigned pr[Q];
@@ -699,7 +735,7 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     // unpacks again instead of the compiler keeping the moments pass's 2Q
     // unpacked values alive (it emits no instruction)
     static_for<Q>([&](auto I) { asm volatile("" : "+r"(pr[decltype(I)::value])); });
-    relax_store<LAT, S, C, IDX32, false>([&](auto I) { return lo(pr[decltype(I)::value]); },
+    relax_store<LAT, S, C, SIDX32, false>([&](auto I) { return lo(pr[decltype(I)::value]); },
                                          [&](auto I) { return hi(pr[decltype(I)::value]); },
                                          [](auto) { return ConvGH<C>{C(0), C(0)}; }, a, drho, u, dT, dst, ps, cell);
   } else if constexpr (STAGE == 3) {
@@ -718,9 +754,9 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     // volatile: the moments pass and the relaxation pass each read h_i from
     // shared memory, so the 107 h values are not all held in registers
     const volatile S* shv = sh;
-    collide_store<LAT, S, C, IDX32>([&](auto I) { return g[decltype(I)::value]; },
-                             [&](auto I) { return static_cast<C>(shv[decltype(I)::value * BX + t]); }, a, dst, ps,
-                             cell);
+    collide_store<LAT, S, C, SIDX32>([&](auto I) { return g[decltype(I)::value]; },
+                                     [&](auto I) { return static_cast<C>(shv[decltype(I)::value * BX + t]); }, a,
+                                     dst, ps, cell);
   } else {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* sg = reinterpret_cast<S*>(smem_raw);  // [2Q][BX]
@@ -747,7 +783,7 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     // every staged value in registers
     if constexpr (IsS16<S>::value) {
       const volatile unsigned* sp = reinterpret_cast<const volatile unsigned*>(smem_raw);
-      collide_store<LAT, S, C, IDX32>(
+      collide_store<LAT, S, C, SIDX32>(
           [&](auto I) {
             float lo, hi;
             unpack16<S>(sp[decltype(I)::value * BX + t], lo, hi);
@@ -761,16 +797,27 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
           a, dst, ps, cell);
     } else {
       const volatile S* sgv = sg;
-      collide_store<LAT, S, C, IDX32>(
+      collide_store<LAT, S, C, SIDX32>(
           [&](auto I) { return raw_value<S, C>(sgv[decltype(I)::value * BX + t]); },
           [&](auto I) { return raw_value<S, C>(sgv[(Q + decltype(I)::value) * BX + t]); }, a, dst, ps, cell);
     }
   }
 }
 
+// blocks whose row lies 3 or more cells from every y and z face take the
+// ROW addressing (the branch is uniform over the block); the others, and
+// grids too small to have such rows, the general one
 template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false>
 __global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
-  step_cell<LAT, S, C, STAGE, BX, IDX32>(src, dst, a, blockIdx.x * BX + threadIdx.x, blockIdx.y, blockIdx.z);
+  const int y = blockIdx.y, z = blockIdx.z;
+  // (the per-thread byte offsets of the ROW path are 32-bit: N E < 2^32)
+  constexpr long long E = IsS16<S>::value ? 2 * (long long)sizeof(S) : (long long)sizeof(S);
+  const bool row = y >= 3 && y < a.n[1] - 3 && (Lat<LAT>::D == 2 || (z >= 3 && z < a.n[2] - 3)) &&
+                   (long long)a.n[0] * a.n[1] * a.n[2] * E < (1LL << 32);
+  if (row)
+    step_cell<LAT, S, C, STAGE, BX, IDX32, true>(src, dst, a, blockIdx.x * BX + threadIdx.x, y, z);
+  else
+    step_cell<LAT, S, C, STAGE, BX, IDX32, false>(src, dst, a, blockIdx.x * BX + threadIdx.x, y, z);
 }
 
 // ---------------------------------------------------------------------------

@@ -33,7 +33,7 @@ class Request:
     tau_g: float
     steps: int
     fields: tuple           # (rho, u, T) host arrays
-    rho0: float = 0.0       # reference state of the deviation storage (0 = 1.0)
+    rho0: float = 0.0       # reference state of the deviation storage (0: the precision's default)
     T0: float = 0.0
 
     @property
