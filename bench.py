@@ -93,6 +93,10 @@ WORKLOADS = {
     "periodic3d_f64_small": dict(lattice=1, prec="f64", shape=(64, 64, 64), gamma=1.4, tau_f=0.6, tau_g=0.6,
                                  steps=4, fields="fourier3d",
                                  desc="D3Q107 FP64 periodic 64^3 (profiling case, 0.9 GB state > L2), 4 steps"),
+    "periodic3d_s16f_small": dict(lattice=1, prec="f32_s16f", shape=(96, 96, 96), gamma=1.4, tau_f=0.6,
+                                  tau_g=0.6, steps=10, fields="fourier3d",
+                                  desc="D3Q107 FP16 storage periodic 96^3 (profiling case, 0.4 GB state > L2), "
+                                       "10 steps"),
     "periodic3d_s16f": dict(lattice=1, prec="f32_s16f", shape=(256, 256, 256), gamma=1.4, tau_f=0.6, tau_g=0.6,
                             steps=100, fields="fourier3d",
                             desc="D3Q107 FP32 compute, FP16 deviation storage, periodic 256^3, 100 steps per solve"),
