@@ -134,10 +134,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# the sources that define each recorded kernel (its code and launch shapes)
+KERNEL_SOURCES = {"k_step": ("kernels.cuh", "launch_impl.cuh"),
+                  "k_step_fd": ("kernels.cuh", "launch_impl.cuh", "fd_march.cuh")}
+
+
+def kernel_source_hash(kind="k_step"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1608_06345_gb300", "csrc")
-    for f in ("kernels.cuh", "launch_impl.cuh", "step_inst.cu"):
+    for f in KERNEL_SOURCES[kind]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -152,7 +157,8 @@ def recorded_traffic(key):
     with open(p) as fh:
         d = json.load(fh)
     rec = d.get(key)
-    if not rec or rec.get("src_hash") != kernel_source_hash():
+    kind = "k_step_fd" if key.startswith("k_step_fd") else "k_step"
+    if not rec or rec.get("src_hash") != kernel_source_hash(kind):
         return None
     return rec.get("dram_bytes_per_launch")
 

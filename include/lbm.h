@@ -44,9 +44,10 @@ enum lbm_status {
   LBM_ENOMEM = 2,     /* device or host allocation failed, or caller buffer too small */
   LBM_ECUDA = 3,      /* a CUDA runtime call failed */
   LBM_ENONFINITE = 4, /* a step produced a non-finite density or temperature */
-  LBM_ETIMEOUT = 5,   /* reserved for a bounded device-side wait that gives up; no
-                         kernel of this library waits on the device, so no call
-                         returns it */
+  LBM_ETIMEOUT = 5,   /* a bounded device-side wait gave up: the marched
+                         finite-difference step waited about a second for a row
+                         copy into shared memory (reported by the next
+                         synchronising call, like LBM_ENONFINITE) */
   LBM_EBUSY = 6       /* a pool's memory budget is full */
 };
 
@@ -141,6 +142,17 @@ int lbm_set_graph_steps(lbm_handle h, int steps);
  * lambda (about 0.07 at tau = 0.8 on rough fields; the largest velocity
  * 3 r moves 3 r lambda cells per step).  Asynchronous; plain launches. */
 int lbm_step_fd(lbm_handle h, long n, double lambda);
+
+/* Kernel of lbm_step_fd (execution control; both compute Eq. (16)/(17) with
+ * the same per-value arithmetic and agree to rounding):
+ *  - LBM_FD_AUTO (default): LBM_FD_CELL;
+ *  - LBM_FD_CELL: one thread per cell, every stencil value read from global
+ *    memory;
+ *  - LBM_FD_MARCH: blocks of 32 columns march along y; the lattice's (c, -c)
+ *    pairs are split over the block's warps, each streaming its planes' rows
+ *    through its own shared-memory ring (D2Q37 only; LBM_EINVAL otherwise). */
+enum lbm_fd_kernel { LBM_FD_AUTO = 0, LBM_FD_CELL = 1, LBM_FD_MARCH = 2 };
+int lbm_set_fd_kernel(lbm_handle h, int kernel);
 
 /* rho, u, T of the stored (post-collision) state, Eq. (14)/(15), into host
  * arrays of N, D*N, N doubles.  Synchronises; returns LBM_ENONFINITE if any

@@ -804,20 +804,53 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
   }
 }
 
-// blocks whose row lies 3 or more cells from every y and z face take the
-// ROW addressing (the branch is uniform over the block); the others, and
-// grids too small to have such rows, the general one
-template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false>
+// Rows a launch of k_step covers:
+//   kRowsAll:      every row (block (x, y, z)); a block whose row lies 3 or
+//                  more cells from every y and z face takes the ROW
+//                  addressing (the branch is uniform over the block), the
+//                  others, and grids too small to have such rows, the
+//                  general one.  One kernel, both code paths.
+//   kRowsInterior: only those rows (block (x, y - 3, z - 3)), ROW addressing
+//   kRowsBoundary: only the other rows of a 3D grid (block (x, k): the k-th
+//                  row of the 3-cell z slabs, then of the 3-cell y slabs of
+//                  the interior z), general addressing
+// A 3D grid launches the last two, so each kernel carries one code path and
+// half the instructions compete for the instruction cache.
+constexpr int kRowsAll = 0, kRowsInterior = 1, kRowsBoundary = 2;
+
+__device__ __forceinline__ void boundary_row(int k, int ny, int nz, int& y, int& z) {
+  if (k < 6 * ny) {
+    const int zz = k / ny;
+    z = zz < 3 ? zz : nz - 6 + zz;
+    y = k - zz * ny;
+  } else {
+    const int kk = k - 6 * ny;
+    z = 3 + kk / 6;
+    const int yy = kk - (kk / 6) * 6;
+    y = yy < 3 ? yy : ny - 6 + yy;
+  }
+}
+
+template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false, int ROWS = kRowsAll>
 __global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S* __restrict__ dst, const Args<C> a) {
-  const int y = blockIdx.y, z = blockIdx.z;
-  // (the per-thread byte offsets of the ROW path are 32-bit: N E < 2^32)
-  constexpr long long E = IsS16<S>::value ? 2 * (long long)sizeof(S) : (long long)sizeof(S);
-  const bool row = y >= 3 && y < a.n[1] - 3 && (Lat<LAT>::D == 2 || (z >= 3 && z < a.n[2] - 3)) &&
-                   (long long)a.n[0] * a.n[1] * a.n[2] * E < (1LL << 32);
-  if (row)
-    step_cell<LAT, S, C, STAGE, BX, IDX32, true>(src, dst, a, blockIdx.x * BX + threadIdx.x, y, z);
-  else
-    step_cell<LAT, S, C, STAGE, BX, IDX32, false>(src, dst, a, blockIdx.x * BX + threadIdx.x, y, z);
+  const int x = blockIdx.x * BX + threadIdx.x;
+  if constexpr (ROWS == kRowsInterior) {
+    step_cell<LAT, S, C, STAGE, BX, IDX32, true>(src, dst, a, x, blockIdx.y + 3, blockIdx.z + 3);
+  } else if constexpr (ROWS == kRowsBoundary) {
+    int y, z;
+    boundary_row(blockIdx.y, a.n[1], a.n[2], y, z);
+    step_cell<LAT, S, C, STAGE, BX, IDX32, false>(src, dst, a, x, y, z);
+  } else {
+    const int y = blockIdx.y, z = blockIdx.z;
+    // (the per-thread byte offsets of the ROW path are 32-bit: N E < 2^32)
+    constexpr long long E = IsS16<S>::value ? 2 * (long long)sizeof(S) : (long long)sizeof(S);
+    const bool row = y >= 3 && y < a.n[1] - 3 && (Lat<LAT>::D == 2 || (z >= 3 && z < a.n[2] - 3)) &&
+                     (long long)a.n[0] * a.n[1] * a.n[2] * E < (1LL << 32);
+    if (row)
+      step_cell<LAT, S, C, STAGE, BX, IDX32, true>(src, dst, a, x, y, z);
+    else
+      step_cell<LAT, S, C, STAGE, BX, IDX32, false>(src, dst, a, x, y, z);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -21,31 +21,59 @@ constexpr size_t step_smem() {
   return (STAGE == 0 || STAGE == 6) ? 0 : (STAGE == 3 ? 1 : 2) * sizeof(S) * Lat<LAT>::Q * BX;
 }
 
+// the dynamic shared-memory opt-in is a per-device function attribute: set
+// it once per device (bit d of the mask) for each kernel instance; the mask
+// is atomic because host threads may launch concurrently (setting the
+// attribute twice is harmless)
+template <int LAT, class S, class C, int STAGE, int BX, int MINB, bool IDX32, int ROWS>
+cudaError_t step_smem_opt_in(size_t smem) {
+  static std::atomic<unsigned long long> configured{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !(configured.load(std::memory_order_acquire) & (1ull << dev))) {
+    e = cudaFuncSetAttribute(k_step<LAT, S, C, STAGE, BX, MINB, IDX32, ROWS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) configured.fetch_or(1ull << dev, std::memory_order_release);
+  }
+  return cudaSuccess;
+}
+
+// rows of a 3D grid that lie within 3 cells of a y or z face
+inline long long boundary_rows(int ny, int nz) { return (long long)ny * nz - (long long)(ny - 6) * (nz - 6); }
+
 template <int LAT, class S, class C, int STAGE, int BX, int MINB = 1, bool IDX32 = false>
 cudaError_t launch_step_v(const Instance* inst, const void* src, void* dst, const Args<C>& a,
                           bool configure_only = false) {
-  const dim3 grid((unsigned)((inst->n[0] + BX - 1) / BX), (unsigned)inst->n[1], (unsigned)inst->n[2]);
-  size_t smem = 0;
-  if constexpr (step_smem<LAT, S, STAGE, BX>() != 0) {
-    smem = step_smem<LAT, S, STAGE, BX>();
-    // the shared-memory opt-in is a per-device function attribute: set it
-    // once per device (bit d of the mask) for this template instance; the
-    // mask is atomic because host threads may launch concurrently (setting
-    // the attribute twice is harmless)
-    static std::atomic<unsigned long long> configured{0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+  constexpr size_t smem = step_smem<LAT, S, STAGE, BX>();
+  const unsigned gx = (unsigned)((inst->n[0] + BX - 1) / BX);
+  // a 3D grid with interior rows whose byte offsets fit 32 bits (the ROW
+  // path) runs as an interior and a boundary launch
+  constexpr long long E = IsS16<S>::value ? 2 * (long long)sizeof(S) : (long long)sizeof(S);
+  const int ny = inst->n[1], nz = inst->n[2];
+  const bool split = Lat<LAT>::D == 3 && ny >= 7 && nz >= 7 && inst->N * E < (1LL << 32) &&
+                     boundary_rows(ny, nz) <= 65535;
+  if constexpr (smem != 0) {
+    cudaError_t e = split ? step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsInterior>(smem)
+                          : step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsAll>(smem);
+    if (e == cudaSuccess && split) e = step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsBoundary>(smem);
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !(configured.load(std::memory_order_acquire) & (1ull << dev))) {
-      e = cudaFuncSetAttribute(k_step<LAT, S, C, STAGE, BX, MINB, IDX32>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      if (dev < 64) configured.fetch_or(1ull << dev, std::memory_order_release);
-    }
   }
   if (configure_only) return cudaSuccess;
-  k_step<LAT, S, C, STAGE, BX, MINB, IDX32><<<grid, BX, smem, inst->stream>>>(static_cast<const S*>(src), static_cast<S*>(dst),
-                                                                  a);
+  const S* s = static_cast<const S*>(src);
+  S* d = static_cast<S*>(dst);
+  if (split) {
+    k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsInterior>
+        <<<dim3(gx, (unsigned)(ny - 6), (unsigned)(nz - 6)), BX, smem, inst->stream>>>(s, d, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsBoundary>
+        <<<dim3(gx, (unsigned)boundary_rows(ny, nz), 1), BX, smem, inst->stream>>>(s, d, a);
+    return cudaGetLastError();
+  }
+  k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsAll>
+      <<<dim3(gx, (unsigned)ny, (unsigned)nz), BX, smem, inst->stream>>>(s, d, a);
   return cudaGetLastError();
 }
 

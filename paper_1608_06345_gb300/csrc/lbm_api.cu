@@ -164,6 +164,7 @@ int check_status(Instance* I) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
   if (e != cudaSuccess) return cuda_fail(e, "synchronising the instance stream");
   if (flag & 1u) return fail(LBM_ENONFINITE, "a step met a non-finite density or temperature");
+  if (flag & 2u) return fail(LBM_ETIMEOUT, "a step gave up waiting for its shared-memory row copies");
   return LBM_OK;
 }
 
@@ -208,6 +209,7 @@ int prepare_instance(Instance* I, int lattice, double gamma, double tau_f, doubl
   if (resolve_reference(grid->prec, grid->rho0, grid->T0, &I->rho0, &I->T0) != LBM_OK)
     return fail(LBM_EINVAL, "16-bit storage needs a positive reference density rho0 (rho0 < 0 asks for whole storage)");
   I->shape = default_shape(lattice, grid->prec);
+  I->fd_kernel = LBM_FD_AUTO;
   I->graph_steps = 64;
   I->graph_shape = -1;
   I->graph_exec = nullptr;
@@ -420,6 +422,15 @@ int lbm_step(lbm_handle h, long n) {
     h->cur ^= 1;
     ++h->steps_done;
   }
+  return LBM_OK;
+}
+
+int lbm_set_fd_kernel(lbm_handle h, int kernel) {
+  if (!h) return fail(LBM_EINVAL, "handle is NULL");
+  if (kernel != LBM_FD_AUTO && kernel != LBM_FD_CELL && kernel != LBM_FD_MARCH)
+    return fail(LBM_EINVAL, "kernel must be LBM_FD_AUTO, LBM_FD_CELL or LBM_FD_MARCH");
+  if (kernel == LBM_FD_MARCH && h->D != 2) return fail(LBM_EINVAL, "the marched finite-difference step is 2D only");
+  h->fd_kernel = kernel;
   return LBM_OK;
 }
 

@@ -43,6 +43,7 @@ struct Instance {
   Args<double> ad;
   Args<float> af;
   StepShape shape;
+  int fd_kernel;  // finite-difference step kernel: LBM_FD_AUTO / LBM_FD_CELL / LBM_FD_MARCH
   // CUDA graph of `graph_steps` consecutive steps (even, so the buffers are
   // back in place after a replay); 0 = plain launches
   int graph_steps;

@@ -2,7 +2,7 @@
 // selected at compile time by LBM_LAT (0 = D2Q37, 1 = D3Q107) and LBM_PREC
 // (0 = FP64, 1 = FP32, 2 = FP32 compute / FP16 storage, 3 = FP32 / BF16).
 // The build compiles this file once per pair so the objects build in parallel.
-#include "launch_impl.cuh"
+#include "fd_march.cuh"
 
 #ifndef LBM_LAT
 #error "LBM_LAT must be defined"
@@ -42,7 +42,7 @@ extern const Launchers LBM_CAT(kLaunchers, LBM_LAT, LBM_PREC) = {
     &shape_count_t<LBM_LAT, StoreT>,
     &shape_get_t<LBM_LAT, StoreT>,
     &configure_step_t<LBM_LAT, StoreT, ComputeT>,
-    &launch_step_fd_t<LBM_LAT, StoreT, ComputeT>,
+    &launch_step_fd_any<LBM_LAT, StoreT, ComputeT>,
 };
 
 }  // namespace lbm

@@ -22,6 +22,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EBU
 LBM_D2Q37, LBM_D3Q107 = 0, 1
 LBM_PERIODIC, LBM_ZERO_GRADIENT = 0, 1
 LBM_F64, LBM_F32, LBM_F32_S16F, LBM_F32_S16BF = 0, 1, 2, 3
+LBM_FD_AUTO, LBM_FD_CELL, LBM_FD_MARCH = 0, 1, 2
 
 PREC_NAMES = {"f64": LBM_F64, "f32": LBM_F32, "f32_s16f": LBM_F32_S16F, "f32_s16bf": LBM_F32_S16BF}
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENONFINITE",
@@ -34,7 +35,8 @@ EXPORTS = ["lbm_state_bytes", "lbm_create", "lbm_destroy", "lbm_init", "lbm_init
            "lbm_conserved_noalloc", "lbm_pool_bytes", "lbm_pool_create", "lbm_pool_destroy",
            "lbm_pool_instance_bytes", "lbm_pool_submit", "lbm_pool_run", "lbm_pool_sync", "lbm_pool_poll",
            "lbm_pool_result", "lbm_pool_stats", "lbm_shape_info", "lbm_set_shape", "lbm_get_shape",
-           "lbm_autotune", "lbm_set_graph_steps", "lbm_quadrature", "lbm_step_fd", "lbm_slab_plan",
+           "lbm_autotune", "lbm_set_graph_steps", "lbm_quadrature", "lbm_step_fd", "lbm_set_fd_kernel",
+           "lbm_slab_plan",
            "lbm_slab_pack", "lbm_slab_unpack"]
 
 
@@ -111,6 +113,7 @@ def load(build_if_missing: bool = False):
         "lbm_get_shape": (ctypes.c_int, [vp]),
         "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ip, dp]),
         "lbm_set_graph_steps": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_set_fd_kernel": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_quadrature": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ip, ctypes.c_double, ip,
                                           dp, dp, dp]),
         "lbm_slab_plan": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
@@ -285,6 +288,10 @@ def lbm_set_graph_steps(h, steps):
     return _check(load().lbm_set_graph_steps(h, int(steps)))
 
 
+def lbm_set_fd_kernel(h, kernel):
+    return _check(load().lbm_set_fd_kernel(h, int(kernel)))
+
+
 def lbm_autotune(h, reps=5):
     """(best shape index, microseconds per step)."""
     k, us = ctypes.c_int(), ctypes.c_double()
@@ -402,6 +409,10 @@ class Solver:
     def step_fd(self, n=1, lam=0.05):
         """Finite-difference steps (Sec. III) with lambda = dt/dx."""
         lbm_step_fd(self.h, n, lam)
+
+    def set_fd_kernel(self, kernel):
+        """LBM_FD_AUTO, LBM_FD_CELL or LBM_FD_MARCH (lbm_set_fd_kernel)."""
+        lbm_set_fd_kernel(self.h, kernel)
 
     def moments(self):
         rho = np.zeros(self.N)

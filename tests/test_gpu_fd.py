@@ -3,7 +3,8 @@ third-order upwind convection) against the oracle's, element by element:
 FP64 <= 1e-12, FP32 <= 1e-5 on small-amplitude random fields (lambda = 0.05,
 tau 0.8: inside the scheme's stability range), both boundary kinds, D2Q37 and
 D3Q107; 16-bit storage on the smooth recipe within its stated bounds; totals
-conserved on a periodic box."""
+conserved on a periodic box.  The marched kernel (LBM_FD_MARCH, D2Q37) is
+compared with the per-cell kernel in every storage precision."""
 import numpy as np
 import pytest
 
@@ -36,6 +37,7 @@ def run_pair(lat, shape, bc, prec, steps, fields, tau_f=0.8, tau_g=0.8, lam=LAM,
 CASES = [
     (0, (300, 7), (P, P), 40),
     (0, (131, 5), (ZG, P), 40),
+    (0, (132, 5), (ZG, ZG), 40),
     (0, (64, 1), (P, P), 30),
     (1, (40, 5, 6), (ZG, P, P), 8),
     (1, (9, 7, 5), (P, ZG, ZG), 8),
@@ -97,3 +99,81 @@ def test_fd_16bit_storage_3d(prec, bound):
     got, ref, _, _ = run_pair(1, shape, (P, P, P), prec, 30, fields, tau_f=0.6, tau_g=0.6, lam=0.03)
     e = parity_errors(got, ref, 1.4)
     assert max(e.values()) <= bound, e
+
+
+def run_kernel(shape, bc, prec, steps, fields, kernel, lam=LAM):
+    from paper_1608_06345_gb300 import lbm
+    s = lbm.Solver(0, 1.4, 0.8, 0.7, shape, bc=bc, prec=prec)
+    s.set_fd_kernel(kernel)
+    s.init(*fields)
+    s.step_fd(steps, lam)
+    got = s.moments()
+    s.close()
+    return got
+
+
+# The marched kernel (blocks of 32 columns walk bands of rows; the (c, -c)
+# pairs split over the warps, each streaming its planes through its own
+# shared-memory ring) does each value's arithmetic as the per-cell kernel
+# and sums the moments in another order, so the two agree to rounding: FP64
+# and FP32 within their parity bounds, 16-bit storage within a few units of
+# the stored format's last place.  The shapes cover ragged last strips
+# (300 = 9 x 32 + 12 columns) and one-row bands, open x (clamped stencil
+# columns) with open or periodic y, grids narrower than the stencil's reach,
+# and many strips with multi-row bands.
+MARCH_CASES = [
+    ((300, 7), (P, P), 10),
+    ((131, 9), (ZG, P), 10),
+    ((260, 13), (ZG, ZG), 10),
+    ((8, 9), (P, ZG), 10),
+    ((3, 6), (P, P), 10),
+    ((520, 400), (P, P), 4),
+]
+MARCH_TOL = {0: TOL["f64"], 1: TOL["f32"], 2: 2e-3, 3: 2e-2}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape,bc,steps", MARCH_CASES)
+def test_fd_march_matches_cell_kernel(shape, bc, steps, prec):
+    from paper_1608_06345_gb300 import lbm
+    fields = li.random_fields(int(np.prod(shape)), 2, seed=sum(shape) + prec, u_amp=0.02, rho_amp=0.02,
+                              T_amp=0.02)
+    cell = run_kernel(shape, bc, prec, steps, fields, lbm.LBM_FD_CELL)
+    march = run_kernel(shape, bc, prec, steps, fields, lbm.LBM_FD_MARCH)
+    e = parity_errors(march, cell, 1.4)
+    assert max(e.values()) <= MARCH_TOL[prec], e
+
+
+def test_fd_march_at_bench_shape_matches_cell_kernel():
+    """The bench's finite-difference workload: D2Q37 FP32 4096^2, lambda
+    0.03, tau_f 0.55, tau_g 0.7 on the Fourier recipe, 3 steps with each
+    kernel."""
+    from paper_1608_06345_gb300 import lbm
+    shape = (4096, 4096)
+    fields = li.fourier_fields(shape, seed_u=1, seed_rho=2)
+    res = []
+    for kernel in (lbm.LBM_FD_CELL, lbm.LBM_FD_MARCH):
+        s = lbm.Solver(0, 1.4, 0.55, 0.7, shape, prec=lbm.LBM_F32)
+        s.set_fd_kernel(kernel)
+        s.init(*fields)
+        s.step_fd(3, 0.03)
+        res.append(s.moments())
+        s.close()
+    e = parity_errors(res[1], res[0], 1.4)
+    assert max(e.values()) <= TOL["f32"], e
+
+
+def test_fd_kernel_choice_is_checked():
+    from paper_1608_06345_gb300 import lbm
+    s = lbm.Solver(0, 1.4, 0.8, 0.8, (18, 4), prec=1)
+    with pytest.raises(lbm.LbmError) as ei:
+        s.set_fd_kernel(7)
+    assert ei.value.code == lbm.LBM_EINVAL
+    s.set_fd_kernel(lbm.LBM_FD_CELL)
+    s.set_fd_kernel(lbm.LBM_FD_MARCH)
+    s.close()
+    s = lbm.Solver(1, 1.4, 0.8, 0.8, (8, 8, 8), prec=1)
+    with pytest.raises(lbm.LbmError):
+        s.set_fd_kernel(lbm.LBM_FD_MARCH)
+    s.set_fd_kernel(lbm.LBM_FD_AUTO)
+    s.close()
