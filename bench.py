@@ -330,6 +330,8 @@ def run_ours(args, wl):
     stream = torch.cuda.current_stream()
     solver = lbm.Solver(wl["lattice"], wl["gamma"], wl["tau_f"], wl["tau_g"], shape, bc=wl.get("bc", (0, 0, 0)),
                         prec=prec, stream=stream)
+    if wl.get("scheme") == "fd":
+        solver.set_fd_kernel({"auto": lbm.LBM_FD_AUTO, "cell": lbm.LBM_FD_CELL, "march": lbm.LBM_FD_MARCH}[args.fd_kernel])
     d_rho = torch.from_numpy(rho).to(device)
     d_u = torch.from_numpy(np.ascontiguousarray(u)).to(device)
     d_T = torch.from_numpy(T).to(device)
@@ -453,7 +455,8 @@ def run_ours(args, wl):
         "config": {"workload": wl["desc"], "lattice": "D2Q37" if wl["lattice"] == 0 else "D3Q107",
                    "grid": list(shape), "storage": wl["prec"], "lattice_steps_per_bench_step": S,
                    "parallelism": f"replicas x{world}",
-                   "l2": f"inputs larger than L2: state {2 * N * 2 * Q * word / 1e9:.1f} GB vs 0.13 GB L2"},
+                   "l2": f"inputs larger than L2: state {2 * N * 2 * Q * word / 1e9:.1f} GB vs 0.13 GB L2",
+                   **({"fd_kernel": args.fd_kernel} if wl.get("scheme") == "fd" else {})},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": key, "bytes_per_cell_update": bytes_per_cell,
@@ -463,7 +466,7 @@ def run_ours(args, wl):
                 "d2h_bytes_per_step": (2 + D) * N * 8,
                 "note": "per bench step = one solve through lbm_init (pinned host fields) + lbm_step + "
                         "lbm_moments (pinned host outputs)"},
-        "gpu_launches": args.steps * (S + 2),
+        "gpu_launches": args.steps * (S * step_launches(wl, shape) + 2),
         "clocks": clk,
         "cpu_baseline": cpu,
     }
@@ -504,6 +507,17 @@ CONFIG_RUNS = [
     ("fd2d", 400),              # finite-difference variant 4096^2
     ("sod2d", 100000),          # D2Q37 FP64 Sod 1000x4 (latency bound)
 ]
+
+
+def step_launches(wl, shape):
+    """Kernel launches per lattice step: a 3D grid with interior rows and
+    32-bit byte offsets runs its step as an interior and a border launch."""
+    if len(shape) != 3 or wl.get("scheme") == "fd":
+        return 1
+    nx, ny, nz = shape
+    E = {"f64": 8, "f32": 4, "f32_s16f": 4, "f32_s16bf": 4}[wl["prec"]]
+    border = ny * nz - (ny - 6) * (nz - 6)
+    return 2 if ny >= 7 and nz >= 7 and nx * ny * nz * E < 2 ** 32 and border <= 65535 else 1
 
 
 def roofline_of(wl, N, step_s):
@@ -744,6 +758,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving summary of the default line")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads of the default line")
+    ap.add_argument("--fd-kernel", default="auto", choices=["auto", "cell", "march"],
+                    help="kernel of the finite-difference workloads (lbm_set_fd_kernel)")
     ap.add_argument("--shape", type=int, default=None,
                     help="run this compiled step shape (lbm_shape_info index) instead of autotuning")
     args = ap.parse_args()
