@@ -238,7 +238,8 @@ int lbm_conserved_noalloc(int lattice, int prec, double gamma, double rho0, doub
  * memory (stages 0-3), the velocities of each cell split over 4 warps
  * (stage 4; stage 7 with the per-cell equilibrium coefficients formed once
  * and shared), for 16-bit storage the (g, h) pairs held packed in registers
- * (stage 6), or two lanes per cell, one for c and one for -c of every
+ * (stage 6) or half of them so and half in shared memory (stage 9), or two
+ * lanes per cell, one for c and one for -c of every
  * (c, -c) pair, whose moment sums meet by warp shuffles (stage 8) -- and
  * the cells per thread block); index 0 is the default.
  * lbm_shape_info describes candidate `index` (LBM_EINVAL past the end). */

@@ -610,6 +610,8 @@ __device__ __forceinline__ C raw_value(S v) {
 //   STAGE 6: 16-bit storage, the Q pulled (g_i, h_i) pairs held packed in
 //            registers (one register per direction, half of STAGE 0's) and
 //            unpacked where each pass uses them
+//   STAGE 9: 16-bit storage, half the pairs packed in registers and the
+//            other half staged in shared memory by cp.async (D3Q107)
 // A block covers BX consecutive cells of a row (thread = cell).
 // ---------------------------------------------------------------------------
 // ROW: the block's row (y, z) lies at least 3 cells from every y and z face,
@@ -738,6 +740,50 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
     relax_store<LAT, S, C, SIDX32, false>([&](auto I) { return lo(pr[decltype(I)::value]); },
                                          [&](auto I) { return hi(pr[decltype(I)::value]); },
                                          [](auto) { return ConvGH<C>{C(0), C(0)}; }, a, drho, u, dT, dst, ps, cell);
+  } else if constexpr (STAGE == 9) {
+    // 16-bit storage: the pairs of the first (Q + 1) / 2 directions held
+    // packed in registers (as STAGE 6), the others staged in shared memory
+    // slots [i - NR][thread] by 4-byte cp.async (as STAGE 3 stages h), so a
+    // thread holds about half the registers of STAGE 6
+    static_assert(IsS16<S>::value, "packed pairs need 16-bit storage");
+    constexpr int NR = (Q + 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned* sp = reinterpret_cast<unsigned*>(smem_raw);  // [Q - NR][BX]
+    const int t = threadIdx.x;
+    unsigned pr[NR];
+    static_for<Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (i < NR) {
+        pr[i] = __ldg(reinterpret_cast<const unsigned*>(pptr(i, I)));
+      } else {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(sp + (i - NR) * BX + t);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(pptr(i, I)));
+      }
+    });
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const volatile unsigned* spv = sp;
+    auto word = [&](auto I) -> unsigned {
+      constexpr int i = decltype(I)::value;
+      if constexpr (i < NR) return pr[i];
+      else return spv[(i - NR) * BX + t];
+    };
+    auto lo = [&](auto I) -> C {
+      float l, h;
+      unpack16<S>(word(I), l, h);
+      return static_cast<C>(l);
+    };
+    auto hi = [&](auto I) -> C {
+      float l, h;
+      unpack16<S>(word(I), l, h);
+      return static_cast<C>(h);
+    };
+    C drho, u[3], dT;
+    moments_raw<LAT, C, true>(lo, hi, a, drho, u, dT);
+    if (!(isfinite(drho) && isfinite(dT))) atomicOr(a.flag, 1u);
+    // as STAGE 6: the relaxation pass unpacks the held pairs again
+    static_for<NR>([&](auto I) { asm volatile("" : "+r"(pr[decltype(I)::value])); });
+    relax_store<LAT, S, C, SIDX32, false>(lo, hi, [](auto) { return ConvGH<C>{C(0), C(0)}; }, a, drho, u, dT, dst,
+                                         ps, cell);
   } else if constexpr (STAGE == 3) {
     static_assert(sizeof(S) == 4 || sizeof(S) == 8, "cp.async needs 4- or 8-byte elements");
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -18,6 +18,7 @@ const Args<C>& args_of(const Instance* inst) {
 // g and h (STAGE 1, 2)
 template <int LAT, class S, int STAGE, int BX>
 constexpr size_t step_smem() {
+  if constexpr (STAGE == 9) return sizeof(unsigned) * (Lat<LAT>::Q - (Lat<LAT>::Q + 1) / 2) * BX;
   return (STAGE == 0 || STAGE == 6) ? 0 : (STAGE == 3 ? 1 : 2) * sizeof(S) * Lat<LAT>::Q * BX;
 }
 
@@ -161,7 +162,7 @@ struct StepShapes {
     static const int s2d[5][3] = {{0, 128, 1}, {0, 256, 1}, {0, 64, 1}, {4, 32, 4}, {7, 32, 4}};
     static const int s3f[7][3] = {{3, 64, 6}, {3, 64, 1}, {1, 64, 1}, {4, 32, 6}, {8, 32, 8}, {8, 64, 4}, {3, 128, 3}};
     static const int s3d[4][3] = {{1, 64, 1}, {4, 32, 3}, {4, 32, 2}, {7, 32, 3}};
-    static const int s3h[7][3] = {{6, 64, 6}, {2, 64, 8}, {2, 64, 1}, {4, 32, 6}, {8, 32, 10}, {8, 32, 12}, {6, 128, 3}};
+    static const int s3h[7][3] = {{6, 64, 6}, {9, 256, 2}, {2, 64, 1}, {4, 32, 6}, {8, 32, 10}, {8, 32, 12}, {6, 128, 3}};
     const int(*t)[3] = (LAT == 0) ? (sizeof(S) == 8 ? s2d : (sizeof(S) == 2 ? s2h : s2))
                                   : (sizeof(S) == 4 ? s3f : (sizeof(S) == 8 ? s3d : s3h));
     *stage = t[k][0];
@@ -226,7 +227,7 @@ cudaError_t launch_step_shape(const Instance* inst, const void* src, void* dst, 
     }
   } else {
     switch (k) {
-      case 1: return launch_step_t<LAT, S, C, 2, 64, 8>(inst, src, dst, a, configure_only);
+      case 1: return launch_step_t<LAT, S, C, 9, 256, 2>(inst, src, dst, a, configure_only);
       case 2: return launch_step_t<LAT, S, C, 2, 64>(inst, src, dst, a, configure_only);
       case 3: return launch_step_split<LAT, S, C, 4, 6>(inst, src, dst, a, configure_only);
       case 4: return launch_step_mirror<LAT, S, C, 64, 10, false>(inst, src, dst, a, configure_only);
