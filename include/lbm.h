@@ -44,10 +44,9 @@ enum lbm_status {
   LBM_ENOMEM = 2,     /* device or host allocation failed, or caller buffer too small */
   LBM_ECUDA = 3,      /* a CUDA runtime call failed */
   LBM_ENONFINITE = 4, /* a step produced a non-finite density or temperature */
-  LBM_ETIMEOUT = 5,   /* a bounded device-side wait gave up: the marched
-                         finite-difference step waited about a second for a row
-                         copy into shared memory (reported by the next
-                         synchronising call, like LBM_ENONFINITE) */
+  LBM_ETIMEOUT = 5,   /* reserved for a bounded device-side wait that gives up; no
+                         kernel of this library waits on the device, so no call
+                         returns it */
   LBM_EBUSY = 6       /* a pool's memory budget is full */
 };
 

@@ -621,7 +621,11 @@ __device__ __forceinline__ C raw_value(S v) {
 // 7-entry table of byte offsets); plane and row shifts are uniform, and the
 // stores address the cell through one per-thread pointer plus the uniform
 // plane stride.  The arithmetic is that of the general path.
-template <int LAT, class S, class C, int STAGE, int BX, bool IDX32 = false, bool ROW = false>
+// UNI (with ROW, any row): the row shift of direction i is not -(c_y nx +
+// c_z nx ny) but the block-uniform ysh[c_y + 3] + zsh[c_z + 3], the shifts
+// of the pulled row and plane after the y and z rules; the rows within 3
+// cells of a y or z face take the ROW path's code with these tables.
+template <int LAT, class S, class C, int STAGE, int BX, bool IDX32 = false, bool ROW = false, bool UNI = false>
 __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restrict__ dst, const Args<C>& a, int x,
                                           int y, int z) {
   using L = Lat<LAT>;
@@ -632,7 +636,16 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
   // source offsets for lattice components c = -3..3 (index c + 3); ROW keeps
   // only xb, the byte offset of the pulled x in the cell's own row
   unsigned xo[ROW ? 1 : 7], yo[ROW ? 1 : 7], zo[ROW ? 1 : 7], xb[ROW ? 7 : 1];
+  unsigned ysh[UNI ? 7 : 1], zsh[UNI ? 7 : 1];
   const unsigned rowcell = (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+  if constexpr (UNI) {
+    static_assert(ROW && IDX32, "uniform shift tables extend the 32-bit ROW path");
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      ysh[k] = (unsigned)(pull_coord(y, k - 3, ny, a.bc[1]) - y) * (unsigned)nx;
+      zsh[k] = (L::D == 3) ? (unsigned)(pull_coord(z, k - 3, nz, a.bc[2]) - z) * ((unsigned)nx * (unsigned)ny) : 0u;
+    }
+  }
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
     if constexpr (ROW) {  // element index of the pulled x in the cell's own row (a byte offset without IDX32)
@@ -663,7 +676,10 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
   // arithmetic, else plane base + 64-bit byte offset
   auto pptr = [&](int plane, auto I) -> const char* {
     constexpr int i = decltype(I)::value;
-    if constexpr (ROW && IDX32) {
+    if constexpr (UNI) {
+      const unsigned u = (unsigned)plane * (unsigned)ps + ysh[L::cy(i) + 3] + zsh[L::cz(i) + 3];
+      return reinterpret_cast<const char*>(src) + (size_t)(u + xb[L::cx(i) + 3]) * E;
+    } else if constexpr (ROW && IDX32) {
       // uniform part plane ps - c_y nx - c_z nx ny plus the thread's x index,
       // in unsigned 32-bit arithmetic: the sum is the element index, below 2^32
       const unsigned u = (unsigned)plane * (unsigned)ps - (unsigned)(L::cy(i) * nx) -
@@ -859,7 +875,8 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
 //   kRowsInterior: only those rows (block (x, y - 3, z - 3)), ROW addressing
 //   kRowsBoundary: only the other rows of a 3D grid (block (x, k): the k-th
 //                  row of the 3-cell z slabs, then of the 3-cell y slabs of
-//                  the interior z), general addressing
+//                  the interior z), ROW addressing with block-uniform row
+//                  shift tables (UNI)
 // A 3D grid launches the last two, so each kernel carries one code path and
 // half the instructions compete for the instruction cache.
 constexpr int kRowsAll = 0, kRowsInterior = 1, kRowsBoundary = 2;
@@ -885,7 +902,10 @@ __global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S*
   } else if constexpr (ROWS == kRowsBoundary) {
     int y, z;
     boundary_row(blockIdx.y, a.n[1], a.n[2], y, z);
-    step_cell<LAT, S, C, STAGE, BX, IDX32, false>(src, dst, a, x, y, z);
+    // the ROW path's code with block-uniform row shifts (UNI), where element
+    // indices fit 32 bits; else the general path
+    if constexpr (IDX32) step_cell<LAT, S, C, STAGE, BX, true, true, true>(src, dst, a, x, y, z);
+    else step_cell<LAT, S, C, STAGE, BX, IDX32, false>(src, dst, a, x, y, z);
   } else {
     const int y = blockIdx.y, z = blockIdx.z;
     // (the per-thread byte offsets of the ROW path are 32-bit: N E < 2^32)

@@ -164,7 +164,6 @@ int check_status(Instance* I) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
   if (e != cudaSuccess) return cuda_fail(e, "synchronising the instance stream");
   if (flag & 1u) return fail(LBM_ENONFINITE, "a step met a non-finite density or temperature");
-  if (flag & 2u) return fail(LBM_ETIMEOUT, "a step gave up waiting for its shared-memory row copies");
   return LBM_OK;
 }
 

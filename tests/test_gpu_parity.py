@@ -55,6 +55,11 @@ CASES_3D = [
     ((150, 5, 6), (P, P, P), 1.4, 0.6, 0.6, 12),
     ((20, 3, 4), (ZG, P, P), 1.3, 0.7, 0.8, 15),
     ((9, 7, 5), (P, ZG, ZG), 5.0 / 3.0, 0.6, 0.6, 10),
+    # Ny, Nz >= 7: the step runs as an interior and a border launch (the border
+    # rows pull across y and z faces, wrapped or clamped)
+    ((40, 9, 8), (P, ZG, ZG), 1.4, 0.6, 0.7, 8),
+    ((24, 11, 7), (ZG, P, ZG), 1.3, 0.65, 0.65, 8),
+    ((70, 8, 10), (P, P, P), 1.4, 0.6, 0.6, 8),
 ]
 
 
