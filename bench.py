@@ -510,9 +510,10 @@ CONFIG_RUNS = [
 
 
 def step_launches(wl, shape):
-    """Kernel launches per lattice step: a 3D grid with interior rows and
-    32-bit byte offsets runs its step as an interior and a border launch."""
-    if len(shape) != 3 or wl.get("scheme") == "fd":
+    """Kernel launches per lattice step: a 3D grid with 16-bit storage,
+    interior rows and 32-bit byte offsets runs its step as an interior and a
+    border launch (FP32 storage as one launch)."""
+    if len(shape) != 3 or wl.get("scheme") == "fd" or wl["prec"] != "f32_s16f" and wl["prec"] != "f32_s16bf":
         return 1
     nx, ny, nz = shape
     E = {"f64": 8, "f32": 4, "f32_s16f": 4, "f32_s16bf": 4}[wl["prec"]]

@@ -877,9 +877,11 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ src, S* __restri
 //                  row of the 3-cell z slabs, then of the 3-cell y slabs of
 //                  the interior z), ROW addressing with block-uniform row
 //                  shift tables (UNI)
-// A 3D grid launches the last two, so each kernel carries one code path and
-// half the instructions compete for the instruction cache.
-constexpr int kRowsAll = 0, kRowsInterior = 1, kRowsBoundary = 2;
+//   kRowsUniform:  block (x, y, z) for every row of a 3D grid, all with the
+//                  ROW path's code and block-uniform row shift tables (UNI)
+// A 3D grid launches kRowsUniform (FP32 storage) or kRowsInterior then
+// kRowsBoundary (16-bit storage), so each kernel carries one code path.
+constexpr int kRowsAll = 0, kRowsInterior = 1, kRowsBoundary = 2, kRowsUniform = 3;
 
 __device__ __forceinline__ void boundary_row(int k, int ny, int nz, int& y, int& z) {
   if (k < 6 * ny) {
@@ -899,6 +901,8 @@ __global__ void __launch_bounds__(BX, MINB) k_step(const S* __restrict__ src, S*
   const int x = blockIdx.x * BX + threadIdx.x;
   if constexpr (ROWS == kRowsInterior) {
     step_cell<LAT, S, C, STAGE, BX, IDX32, true>(src, dst, a, x, blockIdx.y + 3, blockIdx.z + 3);
+  } else if constexpr (ROWS == kRowsUniform) {
+    step_cell<LAT, S, C, STAGE, BX, true, true, true>(src, dst, a, x, blockIdx.y, blockIdx.z);
   } else if constexpr (ROWS == kRowsBoundary) {
     int y, z;
     boundary_row(blockIdx.y, a.n[1], a.n[2], y, z);

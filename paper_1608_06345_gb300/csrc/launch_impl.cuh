@@ -50,20 +50,36 @@ cudaError_t launch_step_v(const Instance* inst, const void* src, void* dst, cons
   constexpr size_t smem = step_smem<LAT, S, STAGE, BX>();
   const unsigned gx = (unsigned)((inst->n[0] + BX - 1) / BX);
   // a 3D grid with interior rows whose byte offsets fit 32 bits (the ROW
-  // path) runs as an interior and a boundary launch
+  // path): with FP32 storage and 32-bit element indices one launch whose
+  // every block takes the ROW path's code with block-uniform row shift
+  // tables; otherwise an interior and a boundary launch (measured: the
+  // uniform launch is the faster for FP32 storage, the split for 16-bit)
   constexpr long long E = IsS16<S>::value ? 2 * (long long)sizeof(S) : (long long)sizeof(S);
+  constexpr bool UNIFORM = Lat<LAT>::D == 3 && IDX32 && sizeof(S) == 4 && !IsS16<S>::value;
   const int ny = inst->n[1], nz = inst->n[2];
   const bool split = Lat<LAT>::D == 3 && ny >= 7 && nz >= 7 && inst->N * E < (1LL << 32) &&
                      boundary_rows(ny, nz) <= 65535;
   if constexpr (smem != 0) {
-    cudaError_t e = split ? step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsInterior>(smem)
-                          : step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsAll>(smem);
-    if (e == cudaSuccess && split) e = step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsBoundary>(smem);
+    cudaError_t e;
+    if (split && UNIFORM) {
+      e = step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsUniform>(smem);
+    } else {
+      e = split ? step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsInterior>(smem)
+                : step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsAll>(smem);
+      if (e == cudaSuccess && split) e = step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsBoundary>(smem);
+    }
     if (e != cudaSuccess) return e;
   }
   if (configure_only) return cudaSuccess;
   const S* s = static_cast<const S*>(src);
   S* d = static_cast<S*>(dst);
+  if constexpr (UNIFORM) {
+    if (split) {
+      k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsUniform>
+          <<<dim3(gx, (unsigned)ny, (unsigned)nz), BX, smem, inst->stream>>>(s, d, a);
+      return cudaGetLastError();
+    }
+  }
   if (split) {
     k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsInterior>
         <<<dim3(gx, (unsigned)(ny - 6), (unsigned)(nz - 6)), BX, smem, inst->stream>>>(s, d, a);
