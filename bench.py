@@ -93,6 +93,14 @@ WORKLOADS = {
     "periodic3d_f64_small": dict(lattice=1, prec="f64", shape=(64, 64, 64), gamma=1.4, tau_f=0.6, tau_g=0.6,
                                  steps=4, fields="fourier3d",
                                  desc="D3Q107 FP64 periodic 64^3 (profiling case, 0.9 GB state > L2), 4 steps"),
+    "periodic3d_wide": dict(lattice=1, prec="f32", shape=(256, 48, 48), gamma=1.4, tau_f=0.6, tau_g=0.6, steps=10,
+                            fields="fourier3d",
+                            desc="D3Q107 FP32 periodic 256x48x48 (profiling case with the bench's 256-cell rows, "
+                                 "1.0 GB state > L2), 10 steps"),
+    "periodic3d_s16f_wide": dict(lattice=1, prec="f32_s16f", shape=(256, 48, 48), gamma=1.4, tau_f=0.6,
+                                 tau_g=0.6, steps=10, fields="fourier3d",
+                                 desc="D3Q107 FP16 storage periodic 256x48x48 (profiling case with the bench's "
+                                      "256-cell rows, 0.5 GB state > L2), 10 steps"),
     "periodic3d_s16f_small": dict(lattice=1, prec="f32_s16f", shape=(96, 96, 96), gamma=1.4, tau_f=0.6,
                                   tau_g=0.6, steps=10, fields="fourier3d",
                                   desc="D3Q107 FP16 storage periodic 96^3 (profiling case, 0.4 GB state > L2), "
