@@ -4,7 +4,8 @@ oracle, with the stated error bounds.
 
 Stated bounds (parity norm of tests/parity.py for L-inf; L1 = mean |error|
 over mean |oracle| per field):
-  smooth periodic box (512^2, 8 Fourier modes, 200 steps):
+  smooth periodic box (512^2, 8 Fourier modes, 200 steps), and the 3D
+  recipe on a 48 x 12 x 10 box with zero-gradient y and z ends (L-inf only):
       FP16  L-inf <= 1e-3, L1 <= 5e-4      BF16  L-inf <= 1e-2, L1 <= 5e-3
   the paper's shock tube (1000 x 16, rho 4|1, 180 steps):
       FP16  L-inf <= 5e-2, L1 <= 2e-3      BF16  L-inf <= 0.5,  L1 <= 2e-2
@@ -86,3 +87,17 @@ def test_reference_state_changes_only_the_representation():
     gpu, _ = run_gpu(0, 1.4, 0.6, 0.6, shape, bc, fields, 60, 0, rho0=0.6, T0=1.3)
     e = parity_errors(gpu, ref, 1.4)
     assert max(e.values()) <= 1e-12, e
+
+
+@pytest.mark.parametrize("prec", [S16F, S16BF])
+def test_d3q107_16bit_interior_and_border_launches(prec):
+    """D3Q107 with 16-bit storage on a grid whose step runs as an interior and
+    a border launch (Ny, Nz >= 7), with zero-gradient y and z ends, so the
+    border rows clamp their pulls: the smooth 3D recipe, 20 steps, against
+    the FP64 oracle within the smooth-field bounds."""
+    shape, bc = (48, 12, 10), (ora.PERIODIC, ora.ZERO_GRADIENT, ora.ZERO_GRADIENT)
+    fields = li.fourier_fields(shape, seed_u=3, seed_rho=4, seed_T=5)
+    ref, _ = run_oracle(ora.D3Q107, 1.4, 0.6, 0.6, shape, bc, fields, 20)
+    gpu, _ = run_gpu(1, 1.4, 0.6, 0.6, shape, bc, fields, 20, prec)
+    e = parity_errors(gpu, ref, 1.4)
+    assert max(e.values()) <= BOUNDS[("smooth", prec)][0], e
