@@ -160,11 +160,12 @@ cudaError_t launch_step_mirror(const Instance* inst, const void* src, void* dst,
 //   D2Q37 FP64:        (0,128,1) (0,256,1) (0,64,1)  (4,32,4)  (7,32,4)
 //   D3Q107 FP32:       (3,64,6)  (3,64,1)  (1,64,1)  (4,32,6)  (8,32,8)  (8,64,4)  (3,128,3)
 //   D3Q107 FP64:       (1,64,1)  (4,32,3)  (4,32,2)  (7,32,3)
-//   D3Q107 16-bit:     (6,64,6)  (2,64,8)  (2,64,1)  (4,32,6)  (8,32,10) (8,32,12) (6,128,3)
+//   D3Q107 16-bit:     (6,64,6)  (9,256,2) (2,64,1)  (4,32,6)  (8,32,10) (8,32,12) (6,128,3)
 // Stage 4 is the velocity-split step: 4 warps per block of 32 cells; stage 7
 // the same with the per-cell coefficients formed once by warp 0 and shared.
 // Stage 8 is the mirror-pair step: two lanes per cell (c and -c of every
-// pair), h staged in shared memory for FP32.  The moments of stages 4, 7
+// pair), h staged in shared memory for FP32.  Stage 9 holds half the 16-bit
+// pairs packed in registers and stages the other half in shared memory.  The moments of stages 4, 7
 // and 8 are summed in another order, so their results differ from the
 // other shapes' by rounding; the defaults (index 0) are the shapes the
 // batched pool uses, whose results are bitwise those of a lone instance.
