@@ -59,10 +59,13 @@ cudaError_t launch_step_v(const Instance* inst, const void* src, void* dst, cons
   const int ny = inst->n[1], nz = inst->n[2];
   const bool split = Lat<LAT>::D == 3 && ny >= 7 && nz >= 7 && inst->N * E < (1LL << 32) &&
                      boundary_rows(ny, nz) <= 65535;
+  // (the choice is made at compile time where it can be, so that no kernel
+  // instance is built that a launch never reaches)
   if constexpr (smem != 0) {
     cudaError_t e;
-    if (split && UNIFORM) {
-      e = step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsUniform>(smem);
+    if constexpr (UNIFORM) {
+      e = split ? step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsUniform>(smem)
+                : step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsAll>(smem);
     } else {
       e = split ? step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsInterior>(smem)
                 : step_smem_opt_in<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsAll>(smem);
@@ -79,15 +82,16 @@ cudaError_t launch_step_v(const Instance* inst, const void* src, void* dst, cons
           <<<dim3(gx, (unsigned)ny, (unsigned)nz), BX, smem, inst->stream>>>(s, d, a);
       return cudaGetLastError();
     }
-  }
-  if (split) {
-    k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsInterior>
-        <<<dim3(gx, (unsigned)(ny - 6), (unsigned)(nz - 6)), BX, smem, inst->stream>>>(s, d, a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsBoundary>
-        <<<dim3(gx, (unsigned)boundary_rows(ny, nz), 1), BX, smem, inst->stream>>>(s, d, a);
-    return cudaGetLastError();
+  } else if constexpr (Lat<LAT>::D == 3) {
+    if (split) {
+      k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsInterior>
+          <<<dim3(gx, (unsigned)(ny - 6), (unsigned)(nz - 6)), BX, smem, inst->stream>>>(s, d, a);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsBoundary>
+          <<<dim3(gx, (unsigned)boundary_rows(ny, nz), 1), BX, smem, inst->stream>>>(s, d, a);
+      return cudaGetLastError();
+    }
   }
   k_step<LAT, S, C, STAGE, BX, MINB, IDX32, kRowsAll>
       <<<dim3(gx, (unsigned)ny, (unsigned)nz), BX, smem, inst->stream>>>(s, d, a);
